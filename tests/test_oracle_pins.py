@@ -1,0 +1,309 @@
+"""Pins for the CPU oracle: checks against facts the paper and mathematics fix,
+independent of the oracle's own code.
+
+* sorting: brute force over all permutations (output must be 0..n-1), numpy's
+  stable sort (a library routine the definition reduces to), the sorted +
+  permutation invariants of Sec. 4.1;
+* networks: the paper's printed networks (tests/golden) must pass, their stated
+  sizes and depths must be reproduced, and dropping any comparator from a
+  size-optimal network must make it fail;
+* mutation tests compile deliberately broken copies of oracle.c and check that
+  these pins catch each mistake.
+"""
+import ctypes
+import itertools
+import math
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rss
+from paper_2002_05599_gb300 import workloads as wl
+
+
+# ---------------------------------------------------------------- sorting ----
+
+@pytest.mark.parametrize("n", range(2, 8))
+def test_sort_fixed_all_permutations(n):
+    perms = np.array(list(itertools.permutations(range(n))), dtype=np.uint32)
+    out = oracle.sort_fixed(perms.reshape(-1), n).reshape(-1, n)
+    assert (out == np.arange(n, dtype=np.uint32)).all()
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("dist", ["uniform", "fewdistinct", "presorted", "reverse"])
+def test_sort_fixed_matches_numpy(dtype, dist):
+    for n in range(2, 17):
+        keys = wl.fixed_arrays(n, 257, dist, dtype, seed=3 + n)
+        out = oracle.sort_fixed(keys, n)
+        ref = np.sort(keys.reshape(-1, n), axis=1).reshape(-1)
+        assert np.array_equal(out, ref)
+
+
+def _stable_reference(keys, vals, offsets):
+    k = keys.copy()
+    v = None if vals is None else vals.copy()
+    for s in range(offsets.size - 1):
+        a, b = int(offsets[s]), int(offsets[s + 1])
+        order = np.argsort(keys[a:b], kind="stable")
+        k[a:b] = keys[a:b][order]
+        if v is not None:
+            v[a:b] = vals[a:b][order]
+    return k, v
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("keys", ["uniform", "fewdistinct", "zipf"])
+def test_sort_segments_matches_numpy_stable(dtype, keys):
+    k, v, off = wl.segment_batch(400, "geometric", keys, dtype, True, seed=7)
+    got_k, got_v = oracle.sort_segments(k, v, off)
+    ref_k, ref_v = _stable_reference(k, v, off)
+    assert np.array_equal(got_k, ref_k)
+    assert np.array_equal(got_v, ref_v)
+
+
+def test_sort_segments_edge_cases():
+    # empty, length-1, all-equal, max-key and a non-zero first offset;
+    # elements outside the segments must stay untouched
+    keys = np.array([9, 9, 5, 5, 5, 0xFFFFFFFF, 3, 0xFFFFFFFF, 1, 7, 7], dtype=np.uint32)
+    vals = np.arange(keys.size, dtype=np.uint32) + 100
+    off = np.array([2, 2, 3, 5, 8, 8, 10], dtype=np.uint32)
+    got_k, got_v = oracle.sort_segments(keys, vals, off)
+    assert got_k.tolist() == [9, 9, 5, 5, 5, 3, 0xFFFFFFFF, 0xFFFFFFFF, 1, 7, 7]
+    assert got_v.tolist() == [100, 101, 102, 103, 104, 106, 105, 107, 108, 109, 110]
+
+
+def test_sort_segments_stability_brute_force():
+    # all 3^5 sequences over {0,1,2}: output order = (key, original position)
+    seqs = np.array(list(itertools.product(range(3), repeat=5)), dtype=np.uint64)
+    off = np.arange(0, seqs.size + 1, 5, dtype=np.uint32)
+    vals = np.tile(np.arange(5, dtype=np.uint32), len(seqs))
+    k, v = oracle.sort_segments(seqs.reshape(-1), vals, off)
+    for s, seq in enumerate(seqs.tolist()):
+        expect = sorted(range(5), key=lambda i: (seq[i], i))
+        assert v[5 * s:5 * s + 5].tolist() == expect
+        assert k[5 * s:5 * s + 5].tolist() == [seq[i] for i in expect]
+
+
+def test_perm_product_definition_and_invariants():
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, 2**63, size=300, dtype=np.uint64)
+    p, z = oracle.PERM_P, oracle.PERM_Z
+    expect = 1
+    for x in a.tolist():
+        expect = expect * ((z - x) % p) % p
+    assert oracle.perm_product(a, z, p) == expect
+    assert oracle.perm_product(rng.permutation(a), z, p) == expect
+    b = a.copy()
+    b[17] = b[18]  # a planted duplication must change v
+    assert oracle.perm_product(b, z, p) != expect
+    a32 = a.astype(np.uint32)
+    assert oracle.perm_product(a32, z, p) == oracle.perm_product(a32.astype(np.uint64), z, p)
+    # z is bumped until v != 0 (Sec. 4.1)
+    c = np.array([oracle.PERM_Z, 1, 2], dtype=np.uint64)
+    assert oracle.perm_product(c) == 0
+    assert oracle.perm_check_z(c) == oracle.PERM_Z + 1
+
+
+def test_is_sorted_segments():
+    off = np.array([0, 3, 3, 5], dtype=np.uint32)
+    assert oracle.is_sorted_segments(np.array([1, 2, 2, 0, 9], dtype=np.uint64), off)
+    assert not oracle.is_sorted_segments(np.array([1, 2, 2, 9, 8], dtype=np.uint64), off)
+
+
+# --------------------------------------------------------------- networks ----
+
+@pytest.mark.parametrize("name", ["best16", "opt10", "bn6", "bnl16", "bnp16"])
+def test_printed_networks_sort(golden_networks, name):
+    n, facts, levels = golden_networks[name]
+    pairs = [p for lv in levels for p in lv]
+    assert len(pairs) == facts["size"]
+    assert oracle.network_failures_01(n, pairs) == 0
+
+
+@pytest.mark.parametrize("name", ["best16", "opt10"])
+def test_printed_levels_and_depth(golden_networks, name):
+    n, facts, levels = golden_networks[name]
+    assert len(levels) == facts["levels"]
+    for lv in levels:  # a level's comparators share no channel (Sec. 2.1)
+        chans = [c for p in lv for c in p]
+        assert len(chans) == len(set(chans))
+    pairs = [p for lv in levels for p in lv]
+    assert oracle.network_depth(n, pairs) == facts["levels"]
+
+
+def test_depth_small_cases():
+    assert oracle.network_depth(2, [(0, 1)]) == 1
+    assert oracle.network_depth(4, [(0, 1), (2, 3)]) == 1
+    assert oracle.network_depth(3, [(0, 1), (1, 2), (0, 1)]) == 3
+    assert oracle.network_depth(4, [(0, 1), (2, 3), (0, 2), (1, 3), (1, 2)]) == 3
+
+
+@pytest.mark.parametrize("name", ["best16", "opt10"])
+def test_dropping_any_comparator_breaks_best_networks(golden_networks, name):
+    # 29 is the optimal size for n=10 (Sec. 2.1) and 60 the best known for n=16:
+    # no sorting network with one comparator fewer can exist / is known.
+    n, _, levels = golden_networks[name]
+    pairs = [p for lv in levels for p in lv]
+    for c in range(len(pairs)):
+        assert oracle.network_failures_01(n, pairs[:c] + pairs[c + 1:]) > 0
+
+
+def test_perm_and_01_checkers_agree(golden_networks):
+    n, _, levels = golden_networks["opt10"]
+    pairs = [p for lv in levels for p in lv]
+    assert oracle.network_failures_perm(n, pairs) == 0
+    assert oracle.network_failures_perm(n, pairs[:-1]) > 0
+    n6, _, lv6 = golden_networks["bn6"]
+    p6 = [p for lv in lv6 for p in lv]
+    for c in range(len(p6)):
+        broken = p6[:c] + p6[c + 1:]
+        assert (oracle.network_failures_perm(n6, broken) > 0) == \
+               (oracle.network_failures_01(n6, broken) > 0)
+
+
+def test_wide_01_checker_matches_plain(golden_networks):
+    rng = np.random.default_rng(11)
+    for name in ["best16", "opt10", "bnl16"]:
+        n, _, levels = golden_networks[name]
+        pairs = [p for lv in levels for p in lv]
+        for trial in range(4):
+            net = list(pairs)
+            if trial:
+                del net[int(rng.integers(len(net)))]
+            assert oracle.network_failures_01_wide(n, net) == oracle.network_failures_01(n, net)
+
+
+def test_insertion_network_brute_force():
+    # the "bubble" network of Knuth 5.3.4 sorts; its count of 0-1 failures after
+    # removing the last comparator equals a direct count
+    n = 6
+    pairs = [(j, j + 1) for i in range(n - 1, 0, -1) for j in range(i)]
+    assert oracle.network_failures_01(n, pairs) == 0
+    broken = pairs[:-1]
+    direct = 0
+    for v in range(1 << n):
+        x = [(v >> i) & 1 for i in range(n)]
+        for i, j in broken:
+            if x[i] > x[j]:
+                x[i], x[j] = x[j], x[i]
+        direct += any(x[i] > x[i + 1] for i in range(n - 1))
+    assert oracle.network_failures_01(n, broken) == direct
+
+
+# -------------------------------------------------------------------- RSS ----
+
+def test_rss_tree_classification_matches_definition():
+    rng = np.random.default_rng(2)
+    for k in (2, 4, 8, 16, 32):
+        spl = sorted(rng.choice(1000, size=k - 1, replace=False).tolist())
+        tree = rss.heap_tree(spl)
+        assert tree[1] == spl[k // 2 - 1]  # root is s_(k/2)
+        for e in range(-2, 1003):
+            assert rss.classify_tree(e, tree) == rss.classify_definition(e, spl)
+
+
+def test_rss_algorithm1_matches_tree():
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        s = sorted(rng.choice(100, size=3, replace=False).tolist())
+        tree = rss.heap_tree(s)
+        for e in range(-1, 102):
+            assert rss.classify_algorithm1(e, *s) == rss.classify_tree(e, tree)
+
+
+@pytest.mark.parametrize("k,a", [(4, 3), (4, 1), (8, 2), (16, 2), (32, 3)])
+def test_rss_sorts(k, a):
+    rng = np.random.default_rng(k * 10 + a)
+    for length in (17, 33, 100, 256):
+        keys = rng.integers(0, 5, size=length).tolist()  # heavy duplicates
+        items = [(x, i) for i, x in enumerate(keys)]
+        assert rss.rss_sort(items, k, a) == sorted(items)
+
+
+# --------------------------------------------------------------- mutation ----
+
+_MUTATIONS = {
+    # a wrong comparison sign in the fixed-size insertion sort
+    "fixed_sign": ("while (j >= 0 && A[j] > x) {\n                A[j + 1] = A[j];\n                --j;\n            }\n            A[j + 1] = x;\n        }\n    }\n}\n\nvoid oracle_sort_fixed_u64",
+                   "while (j >= 0 && A[j] < x) {\n                A[j + 1] = A[j];\n                --j;\n            }\n            A[j + 1] = x;\n        }\n    }\n}\n\nvoid oracle_sort_fixed_u64"),
+    # an unstable segment sort (moves past equal keys)
+    "seg_unstable": ("while (j >= 0 && A[j] > x) {\n                A[j + 1] = A[j];\n                if (V) V[j + 1] = V[j];\n                --j;\n            }\n            A[j + 1] = x;\n            if (V) V[j + 1] = v;\n        }\n    }\n}\n\nvoid oracle_sort_segments_u64",
+                     "while (j >= 0 && A[j] >= x) {\n                A[j + 1] = A[j];\n                if (V) V[j + 1] = V[j];\n                --j;\n            }\n            A[j + 1] = x;\n            if (V) V[j + 1] = v;\n        }\n    }\n}\n\nvoid oracle_sort_segments_u64"),
+    # payload not moved with its key
+    "seg_payload": ("if (V) V[j + 1] = V[j];\n                --j;\n            }\n            A[j + 1] = x;\n            if (V) V[j + 1] = v;\n        }\n    }\n}\n\nvoid oracle_sort_segments_u64",
+                    "--j;\n            }\n            A[j + 1] = x;\n            if (V) V[j + 1] = v;\n        }\n    }\n}\n\nvoid oracle_sort_segments_u64"),
+    # the network comparator exchanges in the wrong direction
+    "net_direction": ("if (x[lo[c]] > x[hi[c]]) {", "if (x[lo[c]] < x[hi[c]]) {"),
+    # the 0-1 vectors skip the top channel's bit
+    "net_index": ("for (int i = 0; i < n; ++i) x[i] = (int64_t)((v >> i) & 1u);",
+                  "for (int i = 0; i < n; ++i) x[i] = (int64_t)((v >> i) & 1u) * (i + 1 < n);"),
+    # depth forgets the +1 per comparator
+    "depth": ("        l += 1;\n", ""),
+    # the permutation product drops a term
+    "perm": ("    for (uint64_t i = 0; i < len; ++i) {\n        uint64_t ar = a[i] % p;",
+             "    for (uint64_t i = 1; i < len; ++i) {\n        uint64_t ar = a[i] % p;"),
+}
+
+
+def _pins_pass(lib_path, golden):
+    """Run a compact version of the pins above against a given oracle build."""
+    saved = oracle._lib
+    try:
+        oracle._lib = None
+        lib = ctypes.CDLL(lib_path)
+        oracle._lib = None
+        # reuse the argtype setup of the real loader
+        real = oracle._LIB_PATH
+        oracle._LIB_PATH = lib_path
+        oracle._lib = None
+        try:
+            oracle._load()
+        finally:
+            oracle._LIB_PATH = real
+        ok = True
+        keys = wl.fixed_arrays(8, 64, "uniform", np.uint32, seed=9)
+        ok &= np.array_equal(oracle.sort_fixed(keys, 8), np.sort(keys.reshape(-1, 8), 1).reshape(-1))
+        for dt in (np.uint32, np.uint64):
+            k, v, off = wl.segment_batch(200, "geometric", "fewdistinct", dt, True, seed=9)
+            gk, gv = oracle.sort_segments(k, v, off)
+            rk, rv = _stable_reference(k, v, off)
+            ok &= np.array_equal(gk, rk) and np.array_equal(gv, rv)
+        n, facts, levels = golden["opt10"]
+        pairs = [p for lv in levels for p in lv]
+        ok &= oracle.network_failures_01(n, pairs) == 0
+        for c in range(len(pairs)):
+            broken = pairs[:c] + pairs[c + 1:]
+            f = oracle.network_failures_01(n, broken)
+            ok &= f > 0 and f == oracle.network_failures_01_wide(n, broken)
+        ok &= oracle.network_depth(n, pairs) == facts["levels"]
+        a = np.arange(1, 50, dtype=np.uint64)
+        expect = 1
+        for x in a.tolist():
+            expect = expect * ((oracle.PERM_Z - x) % oracle.PERM_P) % oracle.PERM_P
+        ok &= oracle.perm_product(a) == expect
+        del lib
+        return bool(ok)
+    finally:
+        oracle._lib = saved
+
+
+def test_pins_pass_on_real_oracle(golden_networks):
+    assert _pins_pass(oracle.build(), golden_networks)
+
+
+@pytest.mark.parametrize("name", sorted(_MUTATIONS))
+def test_planted_mistake_is_caught(golden_networks, name):
+    src = open(oracle._SRC).read()
+    old, new = _MUTATIONS[name]
+    assert src.count(old) == 1, "mutation anchor not found"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "m.c")
+        so = os.path.join(d, f"libm_{name}.so")
+        open(c, "w").write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", so, c])
+        assert not _pins_pass(so, golden_networks)
