@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of batched small-set sorting on GB300 (one JSON line on stdout).
+
+One step sorts one batch of every workload of the hot path, device-resident:
+  * sweep   -- fixed n = 2..16: 2^24 arrays per n of uniform u32 keys
+               (sn_sort_fixed, one launch per n);
+  * uneven  -- 2^24 CSR segments, lengths geometric(p = 0.15) capped at 256,
+               uniform u64 keys with a u32 payload = original index
+               (sn_sort_segments_u64: plan + one persistent launch);
+  * rss     -- 2^20 segments of 17..256 uniform u32 keys, keys only
+               (rss_sort_segments: plan + one persistent launch).
+Before every step (outside the timed window) the work buffers are restored
+from pristine copies, which also evicts L2 (the step touches ~12 GB, L2 is
+126 MB).  Each step is timed with CUDA events on the launching stream.
+
+value     = sorted keys of all parts and ranks / step time (Gkeys/s).
+roofline  = the fixed-n network kernel (sweep): algorithmic bytes (8 B per u32
+            key: read + write) over its measured time, against the measured
+            HBM copy bandwidth.
+e2e       = the same step through the C ABI with host buffers: pinned
+            host -> device copies of the inputs, the sorts, device -> host
+            copies of the results, all inside the timed region.
+cpu_baseline / --impl reference = the CPU oracle (insertion sort, one core)
+            on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank sorts its own full batch (replicas, weak
+scaling); no data-path collective.  Timing: barrier + synchronize around the
+K timed steps, maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEP_NS = list(range(2, 17))
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "sorted Gkeys/s at 1 GB300 and % of HBM roofline"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=0,
+                    help="divide every workload by 2^scale (debugging only; default full size)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_sizes(scale: int):
+    return {"sweep_count": (1 << 24) >> scale, "uneven_nseg": (1 << 24) >> scale,
+            "rss_nseg": (1 << 20) >> scale}
+
+
+def config_dict(sizes, scale):
+    wl = ("fixed-n sweep n=2..16 x 2^24 arrays u32 uniform + uneven batch 2^24 segments "
+          "geometric(0.15) cap 256 u64 keys + u32 payload + RSS range 2^20 segments 17..256 u32 uniform")
+    if scale:
+        wl += f" (all sizes / 2^{scale})"
+    return {"workload": wl, "sweep_arrays_per_n": sizes["sweep_count"],
+            "uneven_segments": sizes["uneven_nseg"], "rss_segments": sizes["rss_nseg"],
+            "seed": 1, "l2": "inputs larger than L2; buffers restored from pristine copies between steps",
+            "parallelism": "replicas (one independent batch per GPU)"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- our arm ----
+
+def make_inputs(sizes, device, rank):
+    import torch
+    from paper_2002_05599_gb300 import workloads as wl
+    seed = 1 + rank
+    inp = {}
+    for n in SWEEP_NS:
+        inp[f"sweep{n}"] = wl.uniform_keys_torch(sizes["sweep_count"] * n, np.uint32, seed=seed * 1000 + n,
+                                                 device=device)
+    lens = wl.segment_lengths(sizes["uneven_nseg"], "geometric", seed=seed, p=0.15, cap=256)
+    off = wl.offsets_from_lengths(lens)
+    total = int(off[-1])
+    inp["uneven_off"] = torch.from_numpy(off.view(np.int32)).to(device)
+    inp["uneven_keys"] = wl.uniform_keys_torch(total, np.uint64, seed=seed, device=device)
+    inp["uneven_vals"] = torch.arange(total, dtype=torch.int32, device=device)
+    lens = wl.segment_lengths(sizes["rss_nseg"], "uniform", seed=seed + 100, lo=17, hi=256)
+    off = wl.offsets_from_lengths(lens)
+    inp["rss_off"] = torch.from_numpy(off.view(np.int32)).to(device)
+    inp["rss_keys"] = wl.uniform_keys_torch(int(off[-1]), np.uint32, seed=seed + 100, device=device)
+    return inp
+
+
+def part_keys(inp):
+    sweep = sum(inp[f"sweep{n}"].numel() for n in SWEEP_NS)
+    return {"sweep": sweep, "uneven": inp["uneven_keys"].numel(), "rss": inp["rss_keys"].numel()}
+
+
+def part_bytes(inp):
+    """Algorithmic bytes per step: every key / payload read and written once,
+    offsets read once."""
+    sweep = 8 * sum(inp[f"sweep{n}"].numel() for n in SWEEP_NS)
+    uneven = 2 * (8 + 4) * inp["uneven_keys"].numel() + 4 * inp["uneven_off"].numel()
+    rss = 2 * 4 * inp["rss_keys"].numel() + 4 * inp["rss_off"].numel()
+    return {"sweep": sweep, "uneven": uneven, "rss": rss}
+
+
+LAUNCHES_PER_STEP = len(SWEEP_NS) + 2 + 2
+
+
+def run_parts(sn, w, events=None):
+    """One step on the current stream; events[0..3] bracket sweep / uneven / rss."""
+    if events:
+        events[0].record()
+    for n in SWEEP_NS:
+        sn.check(sn.sn_sort_fixed(w[f"sweep{n}"], n), f"sn_sort_fixed n={n}")
+    if events:
+        events[1].record()
+    sn.check(sn.sn_sort_segments_u64(w["uneven_keys"], w["uneven_vals"], w["uneven_off"]), "uneven")
+    if events:
+        events[2].record()
+    sn.check(sn.rss_sort_segments(w["rss_keys"], None, w["rss_off"]), "rss")
+    if events:
+        events[3].record()
+
+
+def bench_ours(args, rank, world, local_rank, dist):
+    import torch
+    import paper_2002_05599_gb300 as sn
+
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    sizes = workload_sizes(args.scale)
+    pristine = make_inputs(sizes, device, rank)
+    work = {k: v.clone() for k, v in pristine.items()}
+    keys = part_keys(pristine)
+    bytes_ = part_bytes(pristine)
+    total_keys = sum(keys.values())
+
+    def restore():
+        for k in ("uneven_keys", "uneven_vals", "rss_keys", *[f"sweep{n}" for n in SWEEP_NS]):
+            work[k].copy_(pristine[k])
+
+    for _ in range(args.warmup):
+        restore()
+        run_parts(sn, work)
+    torch.cuda.synchronize()
+    status = sn.sn_check()
+    sn.check(status, "warm-up")
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        restore()
+        run_parts(sn, work, ev[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop() if sampler else None
+    if dist:
+        dist.barrier()
+    sn.check(sn.sn_check(), "timed steps")
+
+    per = {"sweep": [], "uneven": [], "rss": [], "step": []}
+    for e in ev:
+        a, b, c, d = (e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3]),
+                      e[0].elapsed_time(e[3]))
+        per["sweep"].append(a)
+        per["uneven"].append(b)
+        per["rss"].append(c)
+        per["step"].append(d)
+    ms = {k: statistics.mean(v) for k, v in per.items()}
+    if dist:
+        t = torch.tensor([ms["step"], ms["sweep"], ms["uneven"], ms["rss"]], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = dict(zip(["step", "sweep", "uneven", "rss"], t.tolist()))
+
+    hbm, hbm_src = peaks()
+    sweep_gbs = bytes_["sweep"] / (ms["sweep"] * 1e-3) / 1e9
+    parts = {}
+    for p in ("sweep", "uneven", "rss"):
+        gbs = bytes_[p] / (ms[p] * 1e-3) / 1e9
+        parts[p] = {"ms": round(ms[p], 4), "gkeys_s": round(keys[p] / (ms[p] * 1e-3) / 1e9, 2),
+                    "gb_s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4), "keys": keys[p], "bytes": bytes_[p]}
+
+    result = {
+        "metric": METRIC,
+        "value": round(world * total_keys / (ms["step"] * 1e-3) / 1e9, 3),
+        "unit": "Gkeys/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms["step"], 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": config_dict(sizes, args.scale),
+        "parts": parts,
+        "roofline": {"bound": "hbm", "kernel": "fixed_tma_kernel (n=2..16, sweep)",
+                     "achieved": round(sweep_gbs, 1), "peak": hbm, "peak_source": hbm_src,
+                     "unit": "GB/s", "frac": round(sweep_gbs / hbm, 4), "traffic": None},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_loop": round(wall, 3),
+    }
+
+    if not args.no_e2e:
+        result["e2e"] = bench_e2e(args, sn, pristine, world, dist, device)
+    del work
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(sizes, budget_s=12.0)
+    return result
+
+
+def bench_e2e(args, sn, pristine, world, dist, device):
+    """The same step through the C ABI with host buffers (pinned)."""
+    import torch
+    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in pristine.items()}
+    for k, v in pristine.items():
+        host[k].copy_(v)
+    out = {k: torch.empty_like(host[k], pin_memory=True) for k in host if not k.endswith("_off")}
+    dev = {k: torch.empty_like(v) for k, v in pristine.items()}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = sum(t.numel() * t.element_size() for t in out.values())
+    keys = sum(part_keys(pristine).values())
+
+    def step():
+        for k, v in host.items():
+            dev[k].copy_(v, non_blocking=True)
+        run_parts(sn, dev)
+        for k, v in out.items():
+            v.copy_(dev[k], non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / steps
+    if dist:
+        t = torch.tensor([sec], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    sn.check(sn.sn_check(), "e2e")
+    return {"value": round(world * keys / sec / 1e9, 3), "unit": "Gkeys/s", "ms_per_step": round(sec * 1e3, 3),
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+# ----------------------------------------------------------- CPU oracle -----
+
+def oracle_sample(sizes, frac_shift):
+    """A bounded sample of the step: the same workloads, 2^-frac_shift of the units."""
+    from paper_2002_05599_gb300 import workloads as wl
+    sample = {}
+    cnt = max(1, sizes["sweep_count"] >> frac_shift)
+    for n in SWEEP_NS:
+        sample[f"sweep{n}"] = wl.fixed_arrays(n, cnt, "uniform", np.uint32, seed=1000 + n)
+    k, v, off = wl.segment_batch(max(1, sizes["uneven_nseg"] >> frac_shift), "geometric", "uniform", np.uint64,
+                                 True, seed=1, p=0.15, cap=256)
+    sample["uneven"] = (k, v, off)
+    k, _, off = wl.segment_batch(max(1, sizes["rss_nseg"] >> frac_shift), "uniform", "uniform", np.uint32,
+                                 False, seed=101, lo=17, hi=256)
+    sample["rss"] = (k, None, off)
+    desc = (f"2^-{frac_shift} of every part: {cnt} arrays per n, "
+            f"{sample['uneven'][2].size - 1} uneven segments, {sample['rss'][2].size - 1} RSS segments")
+    return sample, desc
+
+
+def oracle_step(sample):
+    import oracle
+    keys = 0
+    t0 = time.perf_counter()
+    for n in SWEEP_NS:
+        a = sample[f"sweep{n}"]
+        oracle.sort_fixed(a, n)
+        keys += a.size
+    for part in ("uneven", "rss"):
+        k, v, off = sample[part]
+        oracle.sort_segments(k, v, off)
+        keys += k.size
+    return keys, time.perf_counter() - t0
+
+
+def cpu_baseline(sizes, budget_s=12.0):
+    import oracle
+    oracle.build()
+    shift = 10
+    sample, desc = oracle_sample(sizes, shift)
+    keys, sec = oracle_step(sample)
+    # grow the sample (halve the shift) while the run stays within the budget
+    while shift > 4 and sec * 2 < budget_s / 2:
+        shift -= 1
+        sample, desc = oracle_sample(sizes, shift)
+        keys, sec = oracle_step(sample)
+    return {"value": round(keys / sec / 1e9, 5), "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": desc, "seconds": round(sec, 3)}
+
+
+def bench_reference(args, rank, world):
+    """--impl reference: the CPU oracle, timed on the host, on a bounded sample."""
+    import oracle
+    oracle.build()
+    sizes = workload_sizes(args.scale)
+    sample, desc = oracle_sample(sizes, 10)
+    _, probe = oracle_step(sample)
+    # keep the whole run (warm-up + timed) within about two minutes
+    shift = 10
+    while shift > 5 and probe * 2 * (args.steps + args.warmup) < 120:
+        shift -= 1
+        sample, desc = oracle_sample(sizes, shift)
+        _, probe = oracle_step(sample)
+    for _ in range(args.warmup):
+        oracle_step(sample)
+    times, keys = [], 0
+    for _ in range(args.steps):
+        keys, sec = oracle_step(sample)
+        times.append(sec)
+    sec = statistics.mean(times)
+    value = round(keys / sec / 1e9, 5)
+    return {
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": config_dict(sizes, args.scale), "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(bench_reference(args, rank, world)), flush=True)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    res = bench_ours(args, rank, world, local_rank, dist)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,117 @@
+/*
+ * smallsort.h -- C ABI of the GB300 small-set sorting library (libsmallsort.so).
+ *
+ * Sorts huge batches of independent small integer arrays on one GPU with the
+ * methods of Bingmann, Marianczuk and Sanders, "Engineering Faster Sorters for
+ * Small Sets of Items": branch-free sorting networks (compare-exchange as
+ * min/max, Sec. 2) for n <= 16, a 32-lane warp network for 17..32 items, and
+ * Register Sample Sort (Sec. 3) for segments of up to 256 items.
+ *
+ * Conventions shared by every call:
+ *   - Pointers named keys / vals / offsets are DEVICE pointers owned by the
+ *     caller.  The library never frees them and keeps no reference after the
+ *     call's stream work completes.  Elements must be naturally aligned
+ *     (4 bytes for u32, 8 bytes for u64).
+ *   - Every call is asynchronous on `stream` (NULL = legacy default stream).
+ *     Argument errors are returned synchronously, before anything is launched.
+ *     Errors found on the device (offsets, timeouts) are recorded in a
+ *     per-device status word and returned by sn_check().
+ *   - Sorting is ascending by unsigned key.  With payloads, equal keys keep
+ *     their input order (the result is ordered by (key, original position)),
+ *     so every output is unique and deterministic.
+ *   - Calls are thread-safe; concurrent calls on different streams are allowed.
+ */
+#ifndef SMALLSORT_H
+#define SMALLSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *sn_stream_t;
+
+/* Status codes.  Every entry point returns SN_OK (0) or one of these. */
+enum {
+    SN_OK = 0,
+    SN_EINVAL = -1,       /* null pointer with work to do, n outside 2..16   */
+    SN_ERANGE = -2,       /* size overflow; segment longer than 256 or
+                             offsets decreasing (device-detected)            */
+    SN_ENOMEM = -3,       /* device scratch allocation failed                */
+    SN_ECUDA = -4,        /* CUDA runtime / launch error                     */
+    SN_ETIMEOUT = -5,     /* a bounded device-side wait ran out              */
+    SN_EUNSUPPORTED = -6  /* the current device is not an sm_103 GPU          */
+};
+
+/* Longest segment the segmented calls accept. */
+#define SN_MAX_SEGMENT 256
+
+/*
+ * Fixed-size arrays (Sec. 2.2.1: an entry method takes an array A and its size
+ * n; Sec. 4.3 ArrayInRow: many arrays stored back to back).
+ *
+ * keys:  `count` contiguous arrays of `n` keys each (count*n keys), sorted
+ *        ascending in place.  16-byte-aligned `keys` take the TMA-staged path;
+ *        other alignments take a slower direct path, never an error.
+ * n:     2..16, else SN_EINVAL.
+ * count: number of arrays; 0 returns SN_OK without launching.
+ *        count*n must stay below 2^62, else SN_ERANGE.
+ */
+int sn_sort_fixed(uint32_t *keys, int n, uint64_t count, sn_stream_t stream);
+int sn_sort_fixed_u64(uint64_t *keys, int n, uint64_t count, sn_stream_t stream);
+
+/*
+ * CSR segments (spec batching layer; the paper's Sec. 5 suggests
+ * bucketing base cases by size and solving batches of equal size).
+ *
+ * offsets: nseg+1 u32 entries; segment i is keys[offsets[i] .. offsets[i+1]).
+ *          Must be non-decreasing with every length <= 256.  A violation is
+ *          detected on the device: the call then leaves keys and vals
+ *          untouched and sn_check() reports SN_ERANGE.
+ * keys:    sorted ascending within each segment, in place.
+ * vals:    optional (may be NULL) u32 payload, permuted with the keys; ties
+ *          are broken by original position inside the segment.
+ * nseg:    0 returns SN_OK without launching; keys/offsets must be non-NULL
+ *          otherwise (SN_EINVAL).
+ * Routing: segments of 2..16 items use the n-item sorting network,
+ *          17..32 the 32-lane warp network, 33..256 Register Sample Sort,
+ *          all inside one persistent launch that bins segments by size.
+ * Scratch: a few MB of stream-ordered device memory from a library-owned pool
+ *          (SN_ENOMEM if that allocation fails).
+ */
+int sn_sort_segments(uint32_t *keys, uint32_t *vals, const uint32_t *offsets,
+                     uint64_t nseg, sn_stream_t stream);
+int sn_sort_segments_u64(uint64_t *keys, uint32_t *vals, const uint32_t *offsets,
+                         uint64_t nseg, sn_stream_t stream);
+
+/*
+ * Same contract as sn_sort_segments, but every segment longer than 16 items
+ * goes through Register Sample Sort (Sec. 3: splitters from a sorted sample,
+ * branch-free classification into buckets, a network per bucket), with the
+ * networks of Sec. 2 as the base case for segments and buckets of <= 16.
+ */
+int rss_sort_segments(uint32_t *keys, uint32_t *vals, const uint32_t *offsets,
+                      uint64_t nseg, sn_stream_t stream);
+int rss_sort_segments_u64(uint64_t *keys, uint32_t *vals, const uint32_t *offsets,
+                          uint64_t nseg, sn_stream_t stream);
+
+/*
+ * Synchronises `stream`, then returns and clears the device status word of the
+ * current device: SN_ERANGE if a segmented call met bad offsets, SN_ETIMEOUT
+ * if a bounded device wait ran out, SN_ECUDA if the stream reported a CUDA
+ * error, else SN_OK.  The word is shared by all calls on the device, so errors
+ * of concurrent calls on other streams are reported together.
+ */
+int sn_check(sn_stream_t stream);
+
+/* Short English description of a status code (static storage). */
+const char *sn_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMALLSORT_H */

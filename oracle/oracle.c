@@ -243,21 +243,10 @@ int64_t oracle_network_failures_01_wide(int n, const int *lo, const int *hi, int
 
 /* ---- The paper's permutation check (Sec. 4.1) ---- */
 
-/* (a * b) mod p for p < 2^63, by the binary (double-and-add) method. */
+/* (a * b) mod p, exact through a 128-bit product (GCC's unsigned __int128). */
 static uint64_t mulmod(uint64_t a, uint64_t b, uint64_t p)
 {
-    uint64_t r = 0;
-    a %= p;
-    while (b) {
-        if (b & 1u) {
-            r += a;
-            if (r >= p) r -= p;
-        }
-        a += a;
-        if (a >= p) a -= p;
-        b >>= 1;
-    }
-    return r;
+    return (uint64_t)(((unsigned __int128)(a % p) * (unsigned __int128)(b % p)) % p);
 }
 
 /* v = prod_i (z - a_i) mod p, with the subtraction taken mod p; p < 2^63. */

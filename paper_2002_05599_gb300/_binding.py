@@ -1,0 +1,145 @@
+"""ctypes binding of libsmallsort.so (same names as include/smallsort.h).
+
+Marshalling only: tensors become device addresses and element counts, the
+stream defaults to torch's current CUDA stream.  There is no CPU fallback: if
+the library is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+SN_OK = 0
+SN_EINVAL = -1
+SN_ERANGE = -2
+SN_ENOMEM = -3
+SN_ECUDA = -4
+SN_ETIMEOUT = -5
+SN_EUNSUPPORTED = -6
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libsmallsort.so")
+_lib = None
+
+
+class SmallSortError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {sn_status_string(status)} ({status})" if what else
+                         f"{sn_status_string(status)} ({status})")
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def library():
+    """Load libsmallsort.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, U64, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+    lib.sn_sort_fixed.argtypes = [P, I, U64, P]
+    lib.sn_sort_fixed_u64.argtypes = [P, I, U64, P]
+    for name in ("sn_sort_segments", "sn_sort_segments_u64",
+                 "rss_sort_segments", "rss_sort_segments_u64"):
+        getattr(lib, name).argtypes = [P, P, P, U64, P]
+    lib.sn_check.argtypes = [P]
+    lib.sn_status_string.argtypes = [I]
+    lib.sn_status_string.restype = ctypes.c_char_p
+    for name in ("sn_sort_fixed", "sn_sort_fixed_u64", "sn_sort_segments", "sn_sort_segments_u64",
+                 "rss_sort_segments", "rss_sort_segments_u64", "sn_check"):
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _addr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _elems(x, size: int) -> int:
+    if x.element_size() != size:
+        raise ValueError(f"expected {size}-byte elements, got {x.element_size()}")
+    return x.numel()
+
+
+def sn_sort_fixed(keys, n: int, count: int | None = None, stream=None) -> int:
+    """Sort ``count`` contiguous arrays of ``n`` u32 keys in place."""
+    if count is None:
+        count = _elems(keys, 4) // n
+    return library().sn_sort_fixed(_addr(keys), n, count, _stream(stream))
+
+
+def sn_sort_fixed_u64(keys, n: int, count: int | None = None, stream=None) -> int:
+    """Sort ``count`` contiguous arrays of ``n`` u64 keys in place."""
+    if count is None:
+        count = _elems(keys, 8) // n
+    return library().sn_sort_fixed_u64(_addr(keys), n, count, _stream(stream))
+
+
+def _segments(fn, ksize, keys, vals, offsets, nseg, stream):
+    if nseg is None:
+        nseg = _elems(offsets, 4) - 1
+    if not isinstance(keys, int):
+        _elems(keys, ksize)
+    if vals is not None and not isinstance(vals, int):
+        _elems(vals, 4)
+    return fn(_addr(keys), _addr(vals), _addr(offsets), nseg, _stream(stream))
+
+
+def sn_sort_segments(keys, vals, offsets, nseg: int | None = None, stream=None) -> int:
+    return _segments(library().sn_sort_segments, 4, keys, vals, offsets, nseg, stream)
+
+
+def sn_sort_segments_u64(keys, vals, offsets, nseg: int | None = None, stream=None) -> int:
+    return _segments(library().sn_sort_segments_u64, 8, keys, vals, offsets, nseg, stream)
+
+
+def rss_sort_segments(keys, vals, offsets, nseg: int | None = None, stream=None) -> int:
+    return _segments(library().rss_sort_segments, 4, keys, vals, offsets, nseg, stream)
+
+
+def rss_sort_segments_u64(keys, vals, offsets, nseg: int | None = None, stream=None) -> int:
+    return _segments(library().rss_sort_segments_u64, 8, keys, vals, offsets, nseg, stream)
+
+
+def sn_check(stream=None) -> int:
+    """Synchronise the stream; return and clear the device status word."""
+    return library().sn_check(_stream(stream))
+
+
+def sn_status_string(status: int) -> str:
+    try:
+        return library().sn_status_string(status).decode()
+    except RuntimeError:
+        return {0: "ok", -1: "invalid argument", -2: "size or offsets out of range",
+                -3: "device scratch allocation failed", -4: "CUDA error",
+                -5: "bounded device wait timed out", -6: "device not supported"}.get(status, "unknown")
+
+
+def check(status: int, what: str = "") -> None:
+    """Raise SmallSortError unless status is SN_OK."""
+    if status != SN_OK:
+        raise SmallSortError(status, what)

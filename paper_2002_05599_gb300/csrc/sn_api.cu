@@ -1,0 +1,192 @@
+// C ABI of libsmallsort.so (declared in include/smallsort.h): argument
+// checks, per-device state, stream-ordered scratch and the device status word.
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+
+#include "smallsort.h"
+#include "sn_common.cuh"
+#include "sn_internal.h"
+
+namespace sn {
+
+// Per-device status word, OR-ed by kernels (kStatusRange, kStatusTimeout).
+__device__ unsigned g_status;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_init_mu;
+DeviceInfo g_info[kMaxDevices];
+std::atomic<bool> g_ready[kMaxDevices];
+
+int init_device(int dev, DeviceInfo* out) {
+  DeviceInfo d;
+  d.device = dev;
+  if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SN_ECUDA;
+  if (cudaDeviceGetAttribute(&d.cc_major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return SN_ECUDA;
+  if (cudaDeviceGetAttribute(&d.cc_minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return SN_ECUDA;
+  if (d.cc_major != 10 || d.cc_minor != 3) return SN_EUNSUPPORTED;  // built for sm_103a only
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return SN_EUNSUPPORTED;
+  d.status = static_cast<unsigned*>(p);
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  if (cudaMemPoolCreate(&d.pool, &props) != cudaSuccess) return SN_ECUDA;
+  uint64_t keep = ~0ull;  // keep freed scratch in the pool between calls
+  cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  *out = d;
+  return SN_OK;
+}
+
+cudaError_t clear_status(const DeviceInfo& d, cudaStream_t s) {
+  return cudaMemsetAsync(d.status, 0, sizeof(unsigned), s);
+}
+
+}  // namespace
+
+const DeviceInfo* device_info(int* err) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    *err = SN_ECUDA;
+    return nullptr;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    *err = SN_EUNSUPPORTED;
+    return nullptr;
+  }
+  if (!g_ready[dev].load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lock(g_init_mu);
+    if (!g_ready[dev].load(std::memory_order_relaxed)) {
+      const int rc = init_device(dev, &g_info[dev]);
+      if (rc != SN_OK) {
+        *err = rc;
+        return nullptr;
+      }
+      g_ready[dev].store(true, std::memory_order_release);
+    }
+  }
+  *err = SN_OK;
+  return &g_info[dev];
+}
+
+}  // namespace sn
+
+namespace {
+
+template <class K>
+int fixed_entry(K* keys, int n, uint64_t count, sn_stream_t stream,
+                cudaError_t (*launch)(K*, int, uint64_t, cudaStream_t, const sn::DeviceInfo&)) {
+  if (n < 2 || n > 16) return SN_EINVAL;
+  if (count == 0) return SN_OK;
+  if (keys == nullptr) return SN_EINVAL;
+  if (count > (1ull << 62) / static_cast<uint64_t>(n)) return SN_ERANGE;
+  if (reinterpret_cast<uintptr_t>(keys) % sizeof(K) != 0) return SN_EINVAL;
+  int err = SN_OK;
+  const sn::DeviceInfo* d = sn::device_info(&err);
+  if (d == nullptr) return err;
+  return launch(keys, n, count, reinterpret_cast<cudaStream_t>(stream), *d) == cudaSuccess ? SN_OK : SN_ECUDA;
+}
+
+template <class K>
+int segments_entry(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream,
+                   sn::SegMode mode,
+                   cudaError_t (*launch)(K*, uint32_t*, const uint32_t*, uint64_t, sn::SegMode, void*, size_t,
+                                         const sn::SegTuning&, cudaStream_t, const sn::DeviceInfo&)) {
+  if (nseg == 0) return SN_OK;
+  if (keys == nullptr || offsets == nullptr) return SN_EINVAL;
+  if (nseg >= (1ull << 32)) return SN_ERANGE;  // segment indices are 32-bit
+  if (reinterpret_cast<uintptr_t>(keys) % sizeof(K) != 0 || reinterpret_cast<uintptr_t>(offsets) % 4 != 0 ||
+      reinterpret_cast<uintptr_t>(vals) % 4 != 0)
+    return SN_EINVAL;
+  int err = SN_OK;
+  const sn::DeviceInfo* d = sn::device_info(&err);
+  if (d == nullptr) return err;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  sn::SegTuning tun;
+  const size_t bytes = sn::segments_scratch_bytes(nseg, tun);
+  void* scratch = nullptr;
+  if (cudaMallocFromPoolAsync(&scratch, bytes, d->pool, s) != cudaSuccess) {
+    cudaGetLastError();
+    return SN_ENOMEM;
+  }
+  const cudaError_t e = launch(keys, vals, offsets, nseg, mode, scratch, bytes, tun, s, *d);
+  cudaFreeAsync(scratch, s);
+  return e == cudaSuccess ? SN_OK : SN_ECUDA;
+}
+
+}  // namespace
+
+namespace sn {
+
+size_t segments_scratch_bytes(uint64_t nseg, const SegTuning& t) {
+  const uint64_t E = static_cast<uint64_t>(t.tile_units);
+  const uint64_t cap = nseg ? (257ull * (nseg - 1)) / E + 2 : 2;
+  return 256 + ((cap * 4 + 255) & ~static_cast<uint64_t>(255));
+}
+
+}  // namespace sn
+
+extern "C" {
+
+int sn_sort_fixed(uint32_t* keys, int n, uint64_t count, sn_stream_t stream) {
+  return fixed_entry<uint32_t>(keys, n, count, stream, sn::launch_fixed_u32);
+}
+
+int sn_sort_fixed_u64(uint64_t* keys, int n, uint64_t count, sn_stream_t stream) {
+  return fixed_entry<uint64_t>(keys, n, count, stream, sn::launch_fixed_u64);
+}
+
+int sn_sort_segments(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream) {
+  return segments_entry<uint32_t>(keys, vals, offsets, nseg, stream, sn::SegMode::kNetworkWarpRss,
+                                  sn::launch_segments_u32);
+}
+
+int sn_sort_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
+                         sn_stream_t stream) {
+  return segments_entry<uint64_t>(keys, vals, offsets, nseg, stream, sn::SegMode::kNetworkWarpRss,
+                                  sn::launch_segments_u64);
+}
+
+int rss_sort_segments(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream) {
+  return segments_entry<uint32_t>(keys, vals, offsets, nseg, stream, sn::SegMode::kRssOnly,
+                                  sn::launch_segments_u32);
+}
+
+int rss_sort_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
+                          sn_stream_t stream) {
+  return segments_entry<uint64_t>(keys, vals, offsets, nseg, stream, sn::SegMode::kRssOnly,
+                                  sn::launch_segments_u64);
+}
+
+int sn_check(sn_stream_t stream) {
+  int err = SN_OK;
+  const sn::DeviceInfo* d = sn::device_info(&err);
+  if (d == nullptr) return err;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SN_ECUDA;
+  unsigned word = 0;
+  if (cudaMemcpyAsync(&word, d->status, sizeof(word), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SN_ECUDA;
+  if (sn::clear_status(*d, s) != cudaSuccess) return SN_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SN_ECUDA;
+  if (word & sn::kStatusRange) return SN_ERANGE;
+  if (word & sn::kStatusTimeout) return SN_ETIMEOUT;
+  return SN_OK;
+}
+
+const char* sn_status_string(int status) {
+  switch (status) {
+    case SN_OK: return "ok";
+    case SN_EINVAL: return "invalid argument";
+    case SN_ERANGE: return "size or offsets out of range";
+    case SN_ENOMEM: return "device scratch allocation failed";
+    case SN_ECUDA: return "CUDA error";
+    case SN_ETIMEOUT: return "bounded device wait timed out";
+    case SN_EUNSUPPORTED: return "device not supported (needs sm_103)";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

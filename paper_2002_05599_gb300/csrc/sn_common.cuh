@@ -1,0 +1,230 @@
+// Device primitives shared by the sorting kernels (sm_103a).
+//
+// Compare-exchange follows the comparator of Sec. 2.1: after it, the lower
+// channel holds the smaller value.  On the GPU it is a pair of integer
+// min/max (keys only) or one compare and selects (key + index items): no
+// branches, all registers, the GPU counterpart of the paper's conditional-move
+// swaps (Sec. 2.2.2).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "networks_gen.h"
+
+namespace sn {
+
+// ---- status bits written by kernels into the per-device status word ----
+constexpr unsigned kStatusRange = 1u;    // bad offsets / segment too long
+constexpr unsigned kStatusTimeout = 2u;  // a bounded wait ran out
+
+// Bounded mbarrier waits: each try may suspend up to kWaitHintNs; after
+// kWaitMaxTries tries (about two seconds) the wait gives up.
+constexpr uint32_t kWaitHintNs = 100000;
+constexpr int kWaitMaxTries = 20000;
+
+// ------------------------------------------------------------ items -------
+
+// Key + original position, ordered lexicographically: this makes every item
+// distinct and gives a stable result.  For u32 keys it is packed into one u64
+// (key in the high half), so one 64-bit min/max orders it.
+template <class K> struct ItemOf;
+template <> struct ItemOf<uint32_t> {
+  using T = uint64_t;
+  static __device__ __forceinline__ T make(uint32_t key, uint32_t idx) {
+    return (static_cast<uint64_t>(key) << 32) | idx;
+  }
+  static __device__ __forceinline__ uint32_t key(T it) { return static_cast<uint32_t>(it >> 32); }
+  static __device__ __forceinline__ uint32_t idx(T it) { return static_cast<uint32_t>(it); }
+  static __device__ __forceinline__ T sentinel(uint32_t slot) { return make(0xFFFFFFFFu, 0x10000u + slot); }
+};
+
+struct Item64 {
+  uint64_t key;
+  uint32_t idx;
+};
+template <> struct ItemOf<uint64_t> {
+  using T = Item64;
+  static __device__ __forceinline__ T make(uint64_t key, uint32_t idx) { return Item64{key, idx}; }
+  static __device__ __forceinline__ uint64_t key(T it) { return it.key; }
+  static __device__ __forceinline__ uint32_t idx(T it) { return it.idx; }
+  static __device__ __forceinline__ T sentinel(uint32_t slot) {
+    return Item64{0xFFFFFFFFFFFFFFFFull, 0x10000u + slot};
+  }
+};
+
+__device__ __forceinline__ bool item_less(uint64_t a, uint64_t b) { return a < b; }
+__device__ __forceinline__ bool item_less(const Item64& a, const Item64& b) {
+  return a.key < b.key || (a.key == b.key && a.idx < b.idx);
+}
+
+// ------------------------------------------------------ compare-exchange --
+
+__device__ __forceinline__ void ce(uint32_t& a, uint32_t& b) {
+  const uint32_t lo = min(a, b);
+  b = max(a, b);
+  a = lo;
+}
+__device__ __forceinline__ void ce(uint64_t& a, uint64_t& b) {
+  const uint64_t lo = min(a, b);
+  b = max(a, b);
+  a = lo;
+}
+__device__ __forceinline__ void ce(Item64& a, Item64& b) {
+  const bool swap = item_less(b, a);
+  const Item64 lo{swap ? b.key : a.key, swap ? b.idx : a.idx};
+  const Item64 hi{swap ? a.key : b.key, swap ? a.idx : b.idx};
+  a = lo;
+  b = hi;
+}
+
+// Min/max of two items for the warp network: `keep_min` selects the result.
+__device__ __forceinline__ uint32_t pick(uint32_t mine, uint32_t other, bool keep_min) {
+  return keep_min ? min(mine, other) : max(mine, other);
+}
+__device__ __forceinline__ uint64_t pick(uint64_t mine, uint64_t other, bool keep_min) {
+  return keep_min ? min(mine, other) : max(mine, other);
+}
+__device__ __forceinline__ Item64 pick(const Item64& mine, const Item64& other, bool keep_min) {
+  const bool other_smaller = item_less(other, mine);
+  return (other_smaller == keep_min) ? other : mine;
+}
+
+// -------------------------------------------------------- networks --------
+
+// Net<N>::run applies the generated N-channel network to a register array.
+template <int N> struct Net;
+template <> struct Net<0> {
+  template <class T> __device__ __forceinline__ static void run(T*) {}
+};
+template <> struct Net<1> {
+  template <class T> __device__ __forceinline__ static void run(T*) {}
+};
+#define SN_CE_(i, j) ce(k[i], k[j]);
+#define SN_DEFINE_NET(n)                                          \
+  template <> struct Net<n> {                                     \
+    template <class T> __device__ __forceinline__ static void run(T* k) { \
+      SN_NET_##n(SN_CE_)                                          \
+    }                                                             \
+  };
+SN_DEFINE_NET(2)
+SN_DEFINE_NET(3)
+SN_DEFINE_NET(4)
+SN_DEFINE_NET(5)
+SN_DEFINE_NET(6)
+SN_DEFINE_NET(7)
+SN_DEFINE_NET(8)
+SN_DEFINE_NET(9)
+SN_DEFINE_NET(10)
+SN_DEFINE_NET(11)
+SN_DEFINE_NET(12)
+SN_DEFINE_NET(13)
+SN_DEFINE_NET(14)
+SN_DEFINE_NET(15)
+SN_DEFINE_NET(16)
+#undef SN_DEFINE_NET
+#undef SN_CE_
+
+// ------------------------------------------------ warp shuffles -----------
+
+__device__ __forceinline__ uint32_t shfl_xor(uint32_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
+__device__ __forceinline__ uint64_t shfl_xor(uint64_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
+__device__ __forceinline__ Item64 shfl_xor(const Item64& v, int m) {
+  return Item64{__shfl_xor_sync(0xFFFFFFFFu, v.key, m), __shfl_xor_sync(0xFFFFFFFFu, v.idx, m)};
+}
+
+// 32-lane warp network (generated schedule): lane l meets lane l ^ M at every
+// step; the lower lane keeps the smaller item.
+template <class T>
+__device__ __forceinline__ void warp_network32(T& x, int lane) {
+#define SN_WARP_STEP_(M) { const T o = shfl_xor(x, M); x = pick(x, o, lane < (lane ^ (M))); }
+  SN_WARP32_SCHEDULE(SN_WARP_STEP_)
+#undef SN_WARP_STEP_
+}
+
+// ------------------------------------------------ async-proxy PTX ---------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitHintNs)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false after about
+// kWaitMaxTries * kWaitHintNs without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int t = 0; t < kWaitMaxTries; ++t)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 1-D bulk copy global -> shared, completion counted on `bar` (bytes).
+// dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 1-D bulk copy shared -> global in the current bulk group.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until at most N bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Wait until at most N bulk groups are incomplete (writes performed).
+template <int N>
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Order this thread's generic-proxy shared-memory writes before later
+// async-proxy (bulk copy) reads of the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Named barrier over `count` threads (multiple of 32).
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+}  // namespace sn

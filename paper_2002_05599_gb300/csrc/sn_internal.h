@@ -1,0 +1,42 @@
+// Internal host-side interface between the C ABI (sn_api.cu) and the kernel
+// translation units.  Not installed; the public interface is smallsort.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sn {
+
+struct DeviceInfo {
+  int device = -1;
+  int sm_count = 0;
+  int cc_major = 0, cc_minor = 0;
+  unsigned* status = nullptr;  // device address of the status word
+  cudaMemPool_t pool = nullptr;
+};
+
+// Per-device facts, initialised once per device (thread-safe).
+const DeviceInfo* device_info(int* err);
+
+// Fixed-size arrays (sn_fixed.cu).  Return a cudaError_t.
+cudaError_t launch_fixed_u32(uint32_t* keys, int n, uint64_t count, cudaStream_t s, const DeviceInfo& d);
+cudaError_t launch_fixed_u64(uint64_t* keys, int n, uint64_t count, cudaStream_t s, const DeviceInfo& d);
+
+// Segments (sn_segments.cu).
+enum class SegMode : int { kNetworkWarpRss = 0, kRssOnly = 1 };
+
+struct SegTuning {
+  int tile_units = 2048;  // segments + elements per tile (>= 512)
+};
+
+// Device scratch needed for a segmented call with nseg segments.
+size_t segments_scratch_bytes(uint64_t nseg, const SegTuning& t);
+
+cudaError_t launch_segments_u32(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
+                                SegMode mode, void* scratch, size_t scratch_bytes, const SegTuning& t,
+                                cudaStream_t s, const DeviceInfo& d);
+cudaError_t launch_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
+                                SegMode mode, void* scratch, size_t scratch_bytes, const SegTuning& t,
+                                cudaStream_t s, const DeviceInfo& d);
+
+}  // namespace sn

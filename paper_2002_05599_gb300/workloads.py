@@ -142,3 +142,39 @@ def segment_batch(nseg: int, lengths: str = "uniform", keys: str = "uniform",
         raise ValueError(f"unknown key distribution {keys!r}")
     v = np.arange(total, dtype=np.uint32) if with_vals else None
     return k, v, off
+
+
+# ----------------------------------------------------------------------------
+# The same SplitMix64 stream evaluated with torch int64 ops on a device, for
+# full-size benchmark inputs.  Two's-complement int64 arithmetic wraps like
+# u64; right shifts are made logical by masking.
+
+def _as_i64(c: int) -> int:
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def _lsr(x, s: int):
+    return (x >> s) & ((1 << (64 - s)) - 1)
+
+
+def _mix_torch(z):
+    z = (z ^ _lsr(z, 30)) * _as_i64(0xBF58476D1CE4E5B9)
+    z = (z ^ _lsr(z, 27)) * _as_i64(0x94D049BB133111EB)
+    return z ^ _lsr(z, 31)
+
+
+def splitmix64_torch(seed: int, start: int, count: int, device):
+    """Outputs start .. start+count-1 of the SplitMix64 stream as int64 (same bits as splitmix64)."""
+    import torch
+    idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    z = _as_i64(seed & 0xFFFFFFFFFFFFFFFF) + idx * _as_i64(0x9E3779B97F4A7C15)
+    return _mix_torch(z)
+
+
+def uniform_keys_torch(count: int, dtype, seed: int = 1, start: int = 0, device="cuda"):
+    """uniform_keys on a device: int32 (bits of u32) or int64 (bits of u64) tensor."""
+    import torch
+    bits = splitmix64_torch(stream_seed(seed, TAG_KEYS), start, count, device)
+    if np.dtype(dtype) == np.uint32:
+        return _lsr(bits, 32).to(torch.int32)
+    return bits
