@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=int, default=0,
                     help="divide every workload by 2^scale (debugging only; default full size)")
+    ap.add_argument("--parts", default="sweep,uneven,rss",
+                    help="comma-separated subset of sweep,uneven,rss (profiling only; default all)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -181,18 +183,24 @@ def part_bytes(inp):
 LAUNCHES_PER_STEP = len(SWEEP_NS) + 2 + 2
 
 
-def run_parts(sn, w, events=None):
+PARTS = ("sweep", "uneven", "rss")
+
+
+def run_parts(sn, w, events=None, parts=PARTS):
     """One step on the current stream; events[0..3] bracket sweep / uneven / rss."""
     if events:
         events[0].record()
-    for n in SWEEP_NS:
-        sn.check(sn.sn_sort_fixed(w[f"sweep{n}"], n), f"sn_sort_fixed n={n}")
+    if "sweep" in parts:
+        for n in SWEEP_NS:
+            sn.check(sn.sn_sort_fixed(w[f"sweep{n}"], n), f"sn_sort_fixed n={n}")
     if events:
         events[1].record()
-    sn.check(sn.sn_sort_segments_u64(w["uneven_keys"], w["uneven_vals"], w["uneven_off"]), "uneven")
+    if "uneven" in parts:
+        sn.check(sn.sn_sort_segments_u64(w["uneven_keys"], w["uneven_vals"], w["uneven_off"]), "uneven")
     if events:
         events[2].record()
-    sn.check(sn.rss_sort_segments(w["rss_keys"], None, w["rss_off"]), "rss")
+    if "rss" in parts:
+        sn.check(sn.rss_sort_segments(w["rss_keys"], None, w["rss_off"]), "rss")
     if events:
         events[3].record()
 
@@ -214,9 +222,10 @@ def bench_ours(args, rank, world, local_rank, dist):
         for k in ("uneven_keys", "uneven_vals", "rss_keys", *[f"sweep{n}" for n in SWEEP_NS]):
             work[k].copy_(pristine[k])
 
+    parts = tuple(p for p in args.parts.split(",") if p)
     for _ in range(args.warmup):
         restore()
-        run_parts(sn, work)
+        run_parts(sn, work, parts=parts)
     torch.cuda.synchronize()
     status = sn.sn_check()
     sn.check(status, "warm-up")
@@ -232,7 +241,7 @@ def bench_ours(args, rank, world, local_rank, dist):
     t0 = time.perf_counter()
     for k in range(args.steps):
         restore()
-        run_parts(sn, work, ev[k])
+        run_parts(sn, work, ev[k], parts=parts)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clocks = sampler.stop() if sampler else None
@@ -256,11 +265,12 @@ def bench_ours(args, rank, world, local_rank, dist):
 
     hbm, hbm_src = peaks()
     sweep_gbs = bytes_["sweep"] / (ms["sweep"] * 1e-3) / 1e9
-    parts = {}
-    for p in ("sweep", "uneven", "rss"):
+    parts_out = {}
+    for p in parts:
         gbs = bytes_[p] / (ms[p] * 1e-3) / 1e9
-        parts[p] = {"ms": round(ms[p], 4), "gkeys_s": round(keys[p] / (ms[p] * 1e-3) / 1e9, 2),
-                    "gb_s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4), "keys": keys[p], "bytes": bytes_[p]}
+        parts_out[p] = {"ms": round(ms[p], 4), "gkeys_s": round(keys[p] / (ms[p] * 1e-3) / 1e9, 2),
+                        "gb_s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4), "keys": keys[p], "bytes": bytes_[p]}
+    total_keys = sum(keys[p] for p in parts)
 
     result = {
         "metric": METRIC,
@@ -276,7 +286,7 @@ def bench_ours(args, rank, world, local_rank, dist):
         "dtype": "u32",
         "data": "synthetic",
         "config": config_dict(sizes, args.scale),
-        "parts": parts,
+        "parts": parts_out,
         "roofline": {"bound": "hbm", "kernel": "fixed_tma_kernel (n=2..16, sweep)",
                      "achieved": round(sweep_gbs, 1), "peak": hbm, "peak_source": hbm_src,
                      "unit": "GB/s", "frac": round(sweep_gbs / hbm, 4), "traffic": None},

@@ -18,10 +18,9 @@ namespace sn {
 constexpr unsigned kStatusRange = 1u;    // bad offsets / segment too long
 constexpr unsigned kStatusTimeout = 2u;  // a bounded wait ran out
 
-// Bounded mbarrier waits: each try may suspend up to kWaitHintNs; after
-// kWaitMaxTries tries (about two seconds) the wait gives up.
-constexpr uint32_t kWaitHintNs = 100000;
-constexpr int kWaitMaxTries = 20000;
+// Bounded mbarrier waits: a wait gives up after kWaitLimitNs of global time
+// (about two seconds) and reports failure instead of spinning forever.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 // ------------------------------------------------------------ items -------
 
@@ -169,20 +168,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitHintNs)
+      : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete; false after about
-// kWaitMaxTries * kWaitHintNs without completion.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase with the given parity to complete; false once
+// kWaitLimitNs have passed without completion.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int t = 0; t < kWaitMaxTries; ++t)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
 }
 
 // 1-D bulk copy global -> shared, completion counted on `bar` (bytes).

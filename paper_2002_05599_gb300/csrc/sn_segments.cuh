@@ -6,11 +6,11 @@
 // so a tile holds at most E segments and at most E + 256 items.  The kernel
 // validates every segment and records the first segment of each tile.
 //
-// Sort (seg_sort_kernel): one producer warp moves whole tiles (offsets, keys,
-// payload) into shared memory with 1-D bulk copies on a two-stage mbarrier
-// ring.  Eight consumer warps bin the tile's segments by length -- the
-// paper's suggestion (Sec. 5, future work) of bucketing base cases by size and
-// solving batches of identical size -- and then take work items from a shared
+// Sort (seg_sort_kernel, one CTA per SM): one producer warp moves whole tiles
+// (offsets, keys, payload) into shared memory with 1-D bulk copies on a
+// two-stage mbarrier ring.  Sixteen consumer warps bin the tile's segments by
+// length -- the paper's suggestion (Sec. 5) of bucketing base cases by size and
+// solving batches of identical size -- and take work items from a shared
 // counter, largest first:
 //   * 33..256 items (17..256 in RSS-only mode): Register Sample Sort by one
 //     warp (Sec. 3): a sample of 2k items sorted by a network, k-1 splitters
@@ -18,8 +18,12 @@
 //     j <- 2j + [t_j < e] over the splitter tree (Algorithm 1 generalised), a
 //     stable counting scatter in shared memory, and one network per bucket;
 //   * 17..32 items: the 32-lane warp network, one item per lane;
-//   * 2..16 items: 32 segments of the same length at a time, one per lane,
-//     each sorted by the n-item network of Sec. 2 in registers.
+//   * 2..16 items: 32 segments of one size class at a time, one per lane, each
+//     sorted in registers by the class's network (2, 4, 8, 12 or 16 channels,
+//     shorter segments padded with +inf).
+// Few distinct networks keep the instruction working set small: with one
+// network per n, warps running different n thrashed the instruction cache
+// (the GPU analogue of the L1i misses the paper measured in Sec. 4.4 / 4.6).
 // With a payload, items are (key, position) pairs so ties keep input order and
 // the payload is gathered by position at the end.  Sorted tiles go back with
 // bulk stores; the partial 16-byte granules at a tile's two ends, which it
@@ -36,19 +40,38 @@ namespace sn {
 namespace seg {
 namespace {  // internal linkage: each instantiation unit gets its own copy
 
-constexpr int kConsumerWarps = 8;
+constexpr int kConsumerWarps = 16;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;  // + one producer warp
 constexpr int kStages = 2;
 constexpr int kMaxSeg = 256;
 constexpr uint32_t kDone = 0xFFFFFFFFu;
 constexpr int kConsumerBar = 1;  // named barrier id for the consumer warps
+constexpr int kRssMaxBuckets = 64;
 
-// Size classes inside a tile: 2..16 -> network of that size, then the warp
-// network and RSS.
-constexpr int kClsWarp = 17;
-constexpr int kClsRss = 18;
-constexpr int kNumCls = 19;
+// Size classes of a tile, in the order their work items are handed out.
+enum Cls : int {
+  kRss64 = 0, kRss32, kRss16, kRss8,  // Register Sample Sort with k buckets
+  kWarp,                              // 17..32 items, warp network
+  kNet16, kNet12, kNet8, kNet4, kNet2,
+  kNumCls,
+  kSkip = kNumCls                     // 0 or 1 item
+};
+
+__device__ __forceinline__ int seg_class(uint32_t len, bool rss_only) {
+  if (len <= 1) return kSkip;
+  if (len == 2) return kNet2;
+  if (len <= 4) return kNet4;
+  if (len <= 8) return kNet8;
+  if (len <= 12) return kNet12;
+  if (len <= 16) return kNet16;
+  if (len <= 32) return rss_only ? kRss8 : kWarp;
+  if (len <= 64) return kRss16;
+  if (len <= 128) return kRss32;
+  return kRss64;
+}
+
+__device__ __forceinline__ bool cls_is_net(int c) { return c >= kNet16; }
 
 struct Plan {
   unsigned bad;        // offsets failed validation
@@ -89,49 +112,36 @@ struct Layout {
   }
   __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
   __host__ __device__ static size_t align128(size_t x) { return (x + 127) & ~static_cast<size_t>(127); }
-  // per-warp Register Sample Sort scratch
+  // per-warp Register Sample Sort scratch: 256 items + 64 bucket counters
   __host__ __device__ static size_t rss_bytes() {
-    return sizeof(K) == 4 ? (256 + 64 + 32) * 8 + 32 * 4
-                          : (256 + 64 + 32) * 8 + (256 + 64 + 32) * 2 + 32 * 4;
+    return sizeof(K) == 4 ? 256 * 8 + kRssMaxBuckets * 4 : 256 * 8 + 256 * 2 + kRssMaxBuckets * 4;
   }
 };
 
-// Per-warp RSS scratch: items, sample, splitter tree, bucket counters.
+// Per-warp RSS scratch.  The item buffer also holds the sorted sample (slots
+// 0..S-1) and then the splitter tree (slots S..S+k-1) before the scatter
+// overwrites it: classification finishes before the first scatter store.
 template <class K> struct RssMem;
 template <> struct RssMem<uint32_t> {
-  uint64_t* buf;     // 256 packed items
-  uint64_t* sample;  // 64
-  uint64_t* tree;    // 32 (heap order, index 1..k-1)
-  uint32_t* cnt;     // 32
-  __device__ explicit RssMem(unsigned char* p)
-      : buf(reinterpret_cast<uint64_t*>(p)), sample(buf + 256), tree(sample + 64),
-        cnt(reinterpret_cast<uint32_t*>(tree + 32)) {}
-  __device__ static uint64_t get(const uint64_t* a, int i) { return a[i]; }
-  __device__ uint64_t get_buf(int i) const { return buf[i]; }
-  __device__ void set_buf(int i, uint64_t v) { buf[i] = v; }
-  __device__ uint64_t get_sample(int i) const { return sample[i]; }
-  __device__ void set_sample(int i, uint64_t v) { sample[i] = v; }
-  __device__ uint64_t get_tree(int i) const { return tree[i]; }
-  __device__ void set_tree(int i, uint64_t v) { tree[i] = v; }
+  uint64_t* buf;  // 256 packed items
+  uint32_t* cnt;  // 64 bucket counters
+  __device__ __forceinline__ explicit RssMem(unsigned char* p)
+      : buf(reinterpret_cast<uint64_t*>(p)), cnt(reinterpret_cast<uint32_t*>(p + 256 * 8)) {}
+  __device__ __forceinline__ uint64_t get(int i) const { return buf[i]; }
+  __device__ __forceinline__ void set(int i, uint64_t v) const { buf[i] = v; }
 };
 template <> struct RssMem<uint64_t> {
-  uint64_t* buf_k;   // 256
-  uint64_t* sam_k;   // 64
-  uint64_t* tree_k;  // 32
-  uint16_t* buf_i;
-  uint16_t* sam_i;
-  uint16_t* tree_i;
-  uint32_t* cnt;
-  __device__ explicit RssMem(unsigned char* p)
-      : buf_k(reinterpret_cast<uint64_t*>(p)), sam_k(buf_k + 256), tree_k(sam_k + 64),
-        buf_i(reinterpret_cast<uint16_t*>(tree_k + 32)), sam_i(buf_i + 256), tree_i(sam_i + 64),
-        cnt(reinterpret_cast<uint32_t*>(tree_i + 32)) {}
-  __device__ Item64 get_buf(int i) const { return Item64{buf_k[i], buf_i[i]}; }
-  __device__ void set_buf(int i, const Item64& v) { buf_k[i] = v.key; buf_i[i] = static_cast<uint16_t>(v.idx); }
-  __device__ Item64 get_sample(int i) const { return Item64{sam_k[i], sam_i[i]}; }
-  __device__ void set_sample(int i, const Item64& v) { sam_k[i] = v.key; sam_i[i] = static_cast<uint16_t>(v.idx); }
-  __device__ Item64 get_tree(int i) const { return Item64{tree_k[i], tree_i[i]}; }
-  __device__ void set_tree(int i, const Item64& v) { tree_k[i] = v.key; tree_i[i] = static_cast<uint16_t>(v.idx); }
+  uint64_t* key;  // 256
+  uint16_t* idx;  // 256
+  uint32_t* cnt;  // 64
+  __device__ __forceinline__ explicit RssMem(unsigned char* p)
+      : key(reinterpret_cast<uint64_t*>(p)), idx(reinterpret_cast<uint16_t*>(p + 256 * 8)),
+        cnt(reinterpret_cast<uint32_t*>(p + 256 * 10)) {}
+  __device__ __forceinline__ Item64 get(int i) const { return Item64{key[i], idx[i]}; }
+  __device__ __forceinline__ void set(int i, const Item64& v) const {
+    key[i] = v.key;
+    idx[i] = static_cast<uint16_t>(v.idx);
+  }
 };
 
 // ---------------------------------------------------------------- plan -----
@@ -171,59 +181,42 @@ __global__ void __launch_bounds__(256)
 
 // ------------------------------------------------------ per-lane networks --
 
-// Segment of exactly N items at kbuf[p..p+N) (payload at vbuf[pv..pv+N)).
+// Segment of L <= N items at kbuf[p..p+L), padded with +inf to N channels
+// (payload at vbuf[pv..pv+L)).
 template <int N, class K, bool kVals>
-__device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int pv) {
+__device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L) {
   if constexpr (kVals) {
     using IO = ItemOf<K>;
     typename IO::T it[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) it[q] = IO::make(kbuf[p + q], q);
+    for (int q = 0; q < N; ++q) it[q] = q < L ? IO::make(kbuf[p + q], q) : IO::sentinel(q);
     Net<N>::run(it);
     uint32_t v[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) v[q] = vbuf[pv + IO::idx(it[q])];
+    for (int q = 0; q < N; ++q)
+      if (q < L) v[q] = vbuf[pv + IO::idx(it[q])];
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      kbuf[p + q] = IO::key(it[q]);
-      vbuf[pv + q] = v[q];
+      if (q < L) {
+        kbuf[p + q] = IO::key(it[q]);
+        vbuf[pv + q] = v[q];
+      }
     }
   } else {
     K k[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) k[q] = kbuf[p + q];
+    for (int q = 0; q < N; ++q) k[q] = q < L ? kbuf[p + q] : static_cast<K>(~static_cast<K>(0));
     Net<N>::run(k);
 #pragma unroll
-    for (int q = 0; q < N; ++q) kbuf[p + q] = k[q];
-  }
-}
-
-template <class K, bool kVals>
-__device__ __noinline__ void net_segment_dispatch(int n, K* kbuf, uint32_t* vbuf, int p, int pv) {
-  switch (n) {
-    case 2: net_segment<2, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 3: net_segment<3, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 4: net_segment<4, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 5: net_segment<5, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 6: net_segment<6, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 7: net_segment<7, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 8: net_segment<8, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 9: net_segment<9, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 10: net_segment<10, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 11: net_segment<11, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 12: net_segment<12, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 13: net_segment<13, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 14: net_segment<14, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 15: net_segment<15, K, kVals>(kbuf, vbuf, p, pv); break;
-    case 16: net_segment<16, K, kVals>(kbuf, vbuf, p, pv); break;
-    default: break;
+    for (int q = 0; q < N; ++q)
+      if (q < L) kbuf[p + q] = k[q];
   }
 }
 
 // ------------------------------------------------------- warp network ------
 
 template <class K, bool kVals>
-__device__ __noinline__ void warp_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, int lane) {
+__device__ __forceinline__ void warp_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, int lane) {
   if constexpr (kVals) {
     using IO = ItemOf<K>;
     typename IO::T x = lane < L ? IO::make(kbuf[p + lane], lane) : IO::sentinel(lane);
@@ -245,54 +238,41 @@ __device__ __noinline__ void warp_segment(K* kbuf, uint32_t* vbuf, int p, int pv
 
 // --------------------------------------------------- Register Sample Sort --
 
-// One bucket of c (<= N) items at rm.buf[st..st+c), padded to N with +inf.
+// Bucket of c (<= N) items at rm[st..st+c), padded to N with +inf.
 template <int N, class K, bool kVals>
-__device__ __forceinline__ void bucket_network(RssMem<K>& rm, int st, int c) {
+__device__ __forceinline__ void bucket_network(const RssMem<K>& rm, int st, int c) {
   using IO = ItemOf<K>;
   if constexpr (kVals) {
     typename IO::T it[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) it[q] = q < c ? rm.get_buf(st + q) : IO::sentinel(q);
+    for (int q = 0; q < N; ++q) it[q] = q < c ? rm.get(st + q) : IO::sentinel(q);
     Net<N>::run(it);
 #pragma unroll
     for (int q = 0; q < N; ++q)
-      if (q < c) rm.set_buf(st + q, it[q]);
+      if (q < c) rm.set(st + q, it[q]);
   } else {
     // keys only: equal keys are interchangeable, so the network orders keys
-    // alone; the position travels along only to keep the item well formed
-    typename IO::T it[N];
-#pragma unroll
-    for (int q = 0; q < N; ++q) it[q] = q < c ? rm.get_buf(st + q) : IO::sentinel(q);
+    // alone (the stored position is not needed after classification)
     K k[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) k[q] = IO::key(it[q]);
+    for (int q = 0; q < N; ++q) k[q] = q < c ? IO::key(rm.get(st + q)) : static_cast<K>(~static_cast<K>(0));
     Net<N>::run(k);
 #pragma unroll
     for (int q = 0; q < N; ++q)
-      if (q < c) rm.set_buf(st + q, IO::make(k[q], 0));
+      if (q < c) rm.set(st + q, IO::make(k[q], 0));
   }
 }
 
 template <class K, bool kVals>
-__device__ __noinline__ void bucket_network_dispatch(int n, RssMem<K>& rm, int st, int c) {
-  switch (n) {
-    case 2: bucket_network<2, K, kVals>(rm, st, c); break;
-    case 3: bucket_network<3, K, kVals>(rm, st, c); break;
-    case 4: bucket_network<4, K, kVals>(rm, st, c); break;
-    case 5: bucket_network<5, K, kVals>(rm, st, c); break;
-    case 6: bucket_network<6, K, kVals>(rm, st, c); break;
-    case 7: bucket_network<7, K, kVals>(rm, st, c); break;
-    case 8: bucket_network<8, K, kVals>(rm, st, c); break;
-    case 9: bucket_network<9, K, kVals>(rm, st, c); break;
-    case 10: bucket_network<10, K, kVals>(rm, st, c); break;
-    case 11: bucket_network<11, K, kVals>(rm, st, c); break;
-    case 12: bucket_network<12, K, kVals>(rm, st, c); break;
-    case 13: bucket_network<13, K, kVals>(rm, st, c); break;
-    case 14: bucket_network<14, K, kVals>(rm, st, c); break;
-    case 15: bucket_network<15, K, kVals>(rm, st, c); break;
-    case 16: bucket_network<16, K, kVals>(rm, st, c); break;
-    default: break;
-  }
+__device__ __forceinline__ void bucket_network_class(int m, const RssMem<K>& rm, int st, int c) {
+  if (m <= 4)
+    bucket_network<4, K, kVals>(rm, st, c);
+  else if (m <= 8)
+    bucket_network<8, K, kVals>(rm, st, c);
+  else if (m <= 12)
+    bucket_network<12, K, kVals>(rm, st, c);
+  else
+    bucket_network<16, K, kVals>(rm, st, c);
 }
 
 // Comparator `c` of the step with XOR mask `mask` of the ascending bitonic
@@ -304,25 +284,26 @@ __device__ __forceinline__ int bitonic_slot(int c, int mask) {
   return ((c >> b) << (b + 1)) | (c & (h - 1));
 }
 
-// Warp-cooperative ascending bitonic sort of n <= 256 stored items
-// (get/set through accessors), padded virtually to the next power of two with
-// +inf: comparators that reach past n are skipped.
-template <class Get, class Set, class LessT>
-__device__ __forceinline__ void warp_bitonic_smem(int n, int lane, Get get, Set set, LessT less) {
+// Warp-cooperative ascending bitonic sort of n <= 256 stored items at
+// rm[st..st+n), padded virtually to the next power of two with +inf:
+// comparators that reach past n are skipped.
+template <class K, bool kByKey>
+__device__ __forceinline__ void warp_bitonic_smem(const RssMem<K>& rm, int st, int n, int lane) {
+  using IO = ItemOf<K>;
   int P = 1;
   while (P < n) P <<= 1;
   for (int k = 2; k <= P; k <<= 1) {
-    for (int mask = k - 1;; mask = (mask == k - 1) ? (k >> 2) : (mask >> 1)) {
-      if (mask == 0) break;
+    for (int mask = k - 1; mask > 0; mask = (mask == k - 1) ? (k >> 2) : (mask >> 1)) {
       for (int c = lane; c < (P >> 1); c += 32) {
         const int i = bitonic_slot(c, mask);
         const int j = i ^ mask;
         if (j < n) {
-          auto a = get(i);
-          auto b = get(j);
-          if (less(b, a)) {
-            set(i, b);
-            set(j, a);
+          const auto a = rm.get(st + i);
+          const auto b = rm.get(st + j);
+          const bool swap = kByKey ? (IO::key(b) < IO::key(a)) : item_less(b, a);
+          if (swap) {
+            rm.set(st + i, b);
+            rm.set(st + j, a);
           }
         }
       }
@@ -333,35 +314,37 @@ __device__ __forceinline__ void warp_bitonic_smem(int n, int lane, Get get, Set 
 }
 
 template <class K, bool kVals>
-__device__ __noinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, RssMem<K> rm, int lane) {
+__device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, const RssMem<K>& rm,
+                                            int lane) {
   using IO = ItemOf<K>;
   using It = typename IO::T;
   const unsigned kFull = 0xFFFFFFFFu;
 
-  // k buckets with at most 8 expected items each; sample of 2k (oversampling 2)
-  int B = 4;
-  while (B * 8 < L) B <<= 1;
+  // k buckets with at most L/4 expected items each (k in 8..64), sample of 2k
+  int B = 8;
+  while (B * 4 < L) B <<= 1;
   const int logB = __ffs(B) - 1;
   const int S = 2 * B;
 
-  // 1. equidistant sample (this library's reading), sorted by a network
+  // 1. equidistant sample (this library's reading of "a sample subset"),
+  //    sorted by a bitonic network; kept in slots 0..S-1
   for (int q = lane; q < S; q += 32) {
     const int pos = ((2 * q + 1) * L) / (2 * S);
-    rm.set_sample(q, IO::make(kbuf[p + pos], pos));
+    rm.set(q, IO::make(kbuf[p + pos], pos));
   }
   __syncwarp();
-  warp_bitonic_smem(
-      S, lane, [&](int i) { return rm.get_sample(i); }, [&](int i, It v) { rm.set_sample(i, v); },
-      [](const It& a, const It& b) { return item_less(a, b); });
+  warp_bitonic_smem<K, false>(rm, 0, S, lane);
 
-  // 2. splitters s_j = S_{2j} (1-based), stored as a heap-ordered tree
-  if (lane >= 1 && lane < B) {
-    const int d = 31 - __clz(lane);
-    const int pos = lane - (1 << d);
-    const int rank = (2 * pos + 1) * (B >> (d + 1));
-    rm.set_tree(lane, rm.get_sample(2 * rank - 1));
+  // 2. splitters s_j = S_{2j} (1-based), heap-ordered tree in slots S+1..S+k-1
+  for (int node = lane; node < B; node += 32) {
+    if (node >= 1) {
+      const int d = 31 - __clz(node);
+      const int pos = node - (1 << d);
+      const int rank = (2 * pos + 1) * (B >> (d + 1));
+      rm.set(S + node, rm.get(2 * rank - 1));
+    }
   }
-  if (lane < B) rm.cnt[lane] = 0;
+  for (int b = lane; b < B; b += 32) rm.cnt[b] = 0;
   __syncwarp();
 
   // 3. classify (j <- 2j + [t_j < e]) and rank items stably within buckets
@@ -375,7 +358,7 @@ __device__ __noinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv,
       const bool valid = e < L;
       const It x = valid ? IO::make(kbuf[p + e], e) : IO::sentinel(0);
       int j = 1;
-      for (int lv = 0; lv < logB; ++lv) j = 2 * j + (item_less(rm.get_tree(j), x) ? 1 : 0);
+      for (int lv = 0; lv < logB; ++lv) j = 2 * j + (item_less(rm.get(S + j), x) ? 1 : 0);
       const int b = j - B;
       unsigned peers = __ballot_sync(kFull, valid);
       for (int bit = 0; bit < logB; ++bit) {
@@ -391,49 +374,64 @@ __device__ __noinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv,
     }
   }
 
-  // 4. bucket starts (exclusive scan over the k counters)
-  const uint32_t c = lane < B ? rm.cnt[lane] : 0;
-  uint32_t incl = c;
+  // 4. bucket starts: exclusive scan over the k counters, lane l owns buckets
+  //    l and l + 32
+  const uint32_t c0 = lane < B ? rm.cnt[lane] : 0;
+  const uint32_t c1 = lane + 32 < B ? rm.cnt[lane + 32] : 0;
+  uint32_t incl = c0;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const uint32_t y = __shfl_up_sync(kFull, incl, d);
     if (lane >= d) incl += y;
   }
-  const uint32_t start = incl - c;
+  const uint32_t start0 = incl - c0;
+  const uint32_t total0 = __shfl_sync(kFull, incl, 31);
+  uint32_t incl1 = c1;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl1, d);
+    if (lane >= d) incl1 += y;
+  }
+  const uint32_t start1 = total0 + incl1 - c1;
+  __syncwarp();
 
-  // 5. stable scatter into the item buffer
+  // 5. stable scatter into the item buffer (overwrites sample and tree)
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     if (r < rounds) {
       const int e = (r << 5) + lane;
       const int b = static_cast<int>(packed[r] >> 16);
-      const uint32_t st = __shfl_sync(kFull, start, b & 31);
-      if (e < L) rm.set_buf(static_cast<int>(st + (packed[r] & 0xFFFFu)), IO::make(kbuf[p + e], e));
+      const uint32_t s_lo = __shfl_sync(kFull, start0, b & 31);
+      const uint32_t s_hi = __shfl_sync(kFull, start1, b & 31);
+      const uint32_t st = b < 32 ? s_lo : s_hi;
+      if (e < L) rm.set(static_cast<int>(st + (packed[r] & 0xFFFFu)), IO::make(kbuf[p + e], e));
     }
   }
   __syncwarp();
 
-  // 6. finish every bucket with a network: lane b sorts bucket b, all lanes
-  //    padded to the largest bucket; buckets above 16 items (rare) are sorted
-  //    afterwards by the whole warp with a bitonic network
-  const uint32_t maxc = __reduce_max_sync(kFull, c);
+  // 6. finish every bucket with a network: every lane pads its buckets to the
+  //    warp's largest bucket (network of 4, 8, 12 or 16 channels); buckets
+  //    above 16 items (rare) are sorted afterwards by the whole warp
+  const uint32_t maxc = __reduce_max_sync(kFull, max(c0, c1));
   const int m = static_cast<int>(maxc < 16 ? maxc : 16);
-  if (m >= 2 && lane < B && c <= 16) bucket_network_dispatch<K, kVals>(m, rm, static_cast<int>(start), static_cast<int>(c));
+  if (m >= 2) {
+    if (lane < B && c0 <= 16) bucket_network_class<K, kVals>(m, rm, static_cast<int>(start0), static_cast<int>(c0));
+    if (lane + 32 < B && c1 <= 16)
+      bucket_network_class<K, kVals>(m, rm, static_cast<int>(start1), static_cast<int>(c1));
+  }
   __syncwarp();
-  unsigned big = __ballot_sync(kFull, lane < B && c > 16);
-  while (big) {
-    const int b = __ffs(big) - 1;
-    big &= big - 1;
-    const int st = static_cast<int>(__shfl_sync(kFull, start, b));
-    const int cb = static_cast<int>(__shfl_sync(kFull, c, b));
-    if constexpr (kVals) {
-      warp_bitonic_smem(
-          cb, lane, [&](int i) { return rm.get_buf(st + i); }, [&](int i, It v) { rm.set_buf(st + i, v); },
-          [](const It& a, const It& b2) { return item_less(a, b2); });
-    } else {
-      warp_bitonic_smem(
-          cb, lane, [&](int i) { return IO::key(rm.get_buf(st + i)); },
-          [&](int i, K v) { rm.set_buf(st + i, IO::make(v, 0)); }, [](K a, K b2) { return a < b2; });
+  if (maxc > 16) {
+    for (int half = 0; half < 2; ++half) {
+      const uint32_t c = half ? c1 : c0;
+      const uint32_t st0 = half ? start1 : start0;
+      unsigned big = __ballot_sync(kFull, lane + 32 * half < B && c > 16);
+      while (big) {
+        const int b = __ffs(big) - 1;
+        big &= big - 1;
+        const int st = static_cast<int>(__shfl_sync(kFull, st0, b));
+        const int cb = static_cast<int>(__shfl_sync(kFull, c, b));
+        warp_bitonic_smem<K, !kVals>(rm, st, cb, lane);
+      }
     }
   }
   __syncwarp();
@@ -445,7 +443,7 @@ __device__ __noinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv,
     for (int r = 0; r < 8; ++r) {
       const int e = (r << 5) + lane;
       if (r < rounds && e < L) {
-        const It y = rm.get_buf(e);
+        const It y = rm.get(e);
         kbuf[p + e] = IO::key(y);
         vv[r] = vbuf[pv + IO::idx(y)];
       }
@@ -460,7 +458,7 @@ __device__ __noinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv,
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int e = (r << 5) + lane;
-      if (r < rounds && e < L) kbuf[p + e] = IO::key(rm.get_buf(e));
+      if (r < rounds && e < L) kbuf[p + e] = IO::key(rm.get(e));
     }
   }
   __syncwarp();
@@ -481,15 +479,8 @@ __device__ __forceinline__ bool consumers_or(bool pred) {
   return out != 0;
 }
 
-__device__ __forceinline__ int seg_class(uint32_t len, bool rss_only) {
-  if (len <= 1) return 0;
-  if (len <= 16) return static_cast<int>(len);
-  if (len <= 32 && !rss_only) return kClsWarp;
-  return kClsRss;
-}
-
 template <class K, bool kVals, bool kRssOnly>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     seg_sort_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
                     const Plan* plan_c, Plan* plan, const uint32_t* __restrict__ tile_first, uint32_t E,
                     unsigned* status) {
@@ -514,6 +505,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     fence_mbar_init();
   }
+  if (tid < kNumCls) cls_cnt[tid] = 0;
+  if (tid == 0) task_ctr = 0;
   __syncthreads();
 
   // ------------------------------------------------------------ producer --
@@ -527,7 +520,6 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int s = k & 1;
         if (k >= kStages && !mbar_wait(&empty[s], ((k >> 1) - 1) & 1u)) {
           atomicOr(status, kStatusTimeout);
-          meta[s].tile = kDone;  // consumers may be gone; nothing more to do
           break;
         }
         const uint32_t t = atomicAdd(&plan->next_tile, 1u);
@@ -579,9 +571,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 
   // ----------------------------------------------------------- consumers --
-  unsigned char* lists_mem = smem + lay.list_at;
-  uint16_t* seg_list = reinterpret_cast<uint16_t*>(lists_mem);
-  RssMem<K> rm(smem + lay.rss_at + warp * L_::rss_bytes());
+  uint16_t* seg_list = reinterpret_cast<uint16_t*>(smem + lay.list_at);
+  const RssMem<K> rm(smem + lay.rss_at + warp * L_::rss_bytes());
+  const unsigned kFull = 0xFFFFFFFFu;
 
   for (uint32_t k = 0;; ++k) {
     const int s = k & 1;
@@ -598,76 +590,92 @@ __global__ void __launch_bounds__(kThreads, 2)
     K* kbuf = reinterpret_cast<K*>(stage + lay.key_at);
     uint32_t* vbuf = reinterpret_cast<uint32_t*>(stage + lay.val_at);
     const int ns = static_cast<int>(m.s1 - m.s0);
+    const int nrounds = (ns + kConsumers - 1) / kConsumers;
 
-    // --- bin the tile's segments by size class
-    if (tid < kNumCls) {
-      cls_cnt[tid] = 0;
-    }
-    if (tid == 0) task_ctr = 0;
-    named_bar_sync(kConsumerBar, kConsumers);
-    for (int i = tid; i < ns; i += kConsumers) {
-      const int c = seg_class(obuf[i + 1] - obuf[i], kRssOnly);
-      if (c) atomicAdd(&cls_cnt[c], 1u);
+    // --- bin the tile's segments by size class (warp-aggregated counts)
+    for (int r = 0; r < nrounds; ++r) {
+      const int i = r * kConsumers + tid;
+      const int c = i < ns ? seg_class(obuf[i + 1] - obuf[i], kRssOnly) : kSkip;
+#pragma unroll
+      for (int q = 0; q < kNumCls; ++q) {
+        const unsigned mask = __ballot_sync(kFull, c == q);
+        if (mask && lane == __ffs(mask) - 1) atomicAdd(&cls_cnt[q], __popc(mask));
+      }
     }
     named_bar_sync(kConsumerBar, kConsumers);
     if (tid == 0) {
-      // list order: RSS, warp, then networks from 16 down to 2 (largest work first)
       uint32_t at = 0, tasks = 0;
-      const int order[kNumCls - 2] = {kClsRss, kClsWarp, 16, 15, 14, 13, 12, 11, 10, 9, 8, 7, 6, 5, 4, 3, 2};
-      for (int q = 0; q < kNumCls - 2; ++q) {
-        const int c = order[q];
-        cls_base[c] = at;
-        cls_cur[c] = at;
-        at += cls_cnt[c];
+      for (int q = 0; q < kNumCls; ++q) {
+        cls_base[q] = at;
+        cls_cur[q] = at;
+        at += cls_cnt[q];
         task_base[q] = tasks;
-        tasks += (c >= kClsWarp) ? cls_cnt[c] : (cls_cnt[c] + 31) / 32;
+        tasks += cls_is_net(q) ? (cls_cnt[q] + 31) / 32 : cls_cnt[q];
       }
-      task_base[kNumCls - 2] = tasks;
+      task_base[kNumCls] = tasks;
     }
     named_bar_sync(kConsumerBar, kConsumers);
-    for (int i = tid; i < ns; i += kConsumers) {
-      const int c = seg_class(obuf[i + 1] - obuf[i], kRssOnly);
-      if (c) seg_list[atomicAdd(&cls_cur[c], 1u)] = static_cast<uint16_t>(i);
+    for (int r = 0; r < nrounds; ++r) {
+      const int i = r * kConsumers + tid;
+      const int c = i < ns ? seg_class(obuf[i + 1] - obuf[i], kRssOnly) : kSkip;
+#pragma unroll
+      for (int q = 0; q < kNumCls; ++q) {
+        const unsigned mask = __ballot_sync(kFull, c == q);
+        if (mask) {
+          uint32_t at = 0;
+          if (lane == __ffs(mask) - 1) at = atomicAdd(&cls_cur[q], __popc(mask));
+          at = __shfl_sync(kFull, at, __ffs(mask) - 1);
+          if (c == q) seg_list[at + __popc(mask & ((1u << lane) - 1u))] = static_cast<uint16_t>(i);
+        }
+      }
     }
     named_bar_sync(kConsumerBar, kConsumers);
 
-    // --- work items
-    const uint32_t ntasks = task_base[kNumCls - 2];
+    // --- work items, largest classes first
+    const uint32_t ntasks = task_base[kNumCls];
     const uint32_t e0 = m.e0;
     for (;;) {
       uint32_t task = 0;
       if (lane == 0) task = atomicAdd(&task_ctr, 1u);
-      task = __shfl_sync(0xFFFFFFFFu, task, 0);
+      task = __shfl_sync(kFull, task, 0);
       if (task >= ntasks) break;
       int q = 0;
       while (task >= task_base[q + 1]) ++q;
       const uint32_t j = task - task_base[q];
-      if (q == 0 || q == 1) {
-        const int c = (q == 0) ? kClsRss : kClsWarp;
-        const int i = seg_list[cls_base[c] + j];
+      if (!cls_is_net(q)) {
+        const int i = seg_list[cls_base[q] + j];
         const uint32_t o = obuf[i];
         const int L = static_cast<int>(obuf[i + 1] - o);
         const int p = static_cast<int>(o - e0 + m.key_shift);
         const int pv = static_cast<int>(o - e0 + m.val_shift);
-        if (q == 0)
-          rss_segment<K, kVals>(kbuf, vbuf, p, pv, L, rm, lane);
-        else
+        if (q == kWarp)
           warp_segment<K, kVals>(kbuf, vbuf, p, pv, L, lane);
+        else
+          rss_segment<K, kVals>(kbuf, vbuf, p, pv, L, rm, lane);
       } else {
-        const int n = 18 - q;  // q = 2 -> 16 ... q = 16 -> 2
         const uint32_t slot = j * 32 + lane;
-        if (slot < cls_cnt[n]) {
-          const int i = seg_list[cls_base[n] + slot];
+        if (slot < cls_cnt[q]) {
+          const int i = seg_list[cls_base[q] + slot];
           const uint32_t o = obuf[i];
-          net_segment_dispatch<K, kVals>(n, kbuf, vbuf, static_cast<int>(o - e0 + m.key_shift),
-                                         static_cast<int>(o - e0 + m.val_shift));
+          const int L = static_cast<int>(obuf[i + 1] - o);
+          const int p = static_cast<int>(o - e0 + m.key_shift);
+          const int pv = static_cast<int>(o - e0 + m.val_shift);
+          switch (q) {
+            case kNet16: net_segment<16, K, kVals>(kbuf, vbuf, p, pv, L); break;
+            case kNet12: net_segment<12, K, kVals>(kbuf, vbuf, p, pv, L); break;
+            case kNet8: net_segment<8, K, kVals>(kbuf, vbuf, p, pv, L); break;
+            case kNet4: net_segment<4, K, kVals>(kbuf, vbuf, p, pv, L); break;
+            default: net_segment<2, K, kVals>(kbuf, vbuf, p, pv, L); break;
+          }
         }
       }
     }
 
-    // --- store the tile
+    // --- store the tile; reset the counters for the next one
     fence_proxy_async_smem();
     named_bar_sync(kConsumerBar, kConsumers);
+    if (tid < kNumCls) cls_cnt[tid] = 0;
+    if (tid == 32) task_ctr = 0;
     if (m.e1 > m.e0) {
       const uintptr_t kb = reinterpret_cast<uintptr_t>(keys);
       const uintptr_t a = kb + sizeof(K) * m.e0, z = kb + sizeof(K) * m.e1;
@@ -757,6 +765,7 @@ cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, ui
                             void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
                             const DeviceInfo& d) {
   if (scratch_bytes < segments_scratch_bytes(nseg, t)) return cudaErrorInvalidValue;
+  if (t.tile_units < 512 || t.tile_units > 8192) return cudaErrorInvalidValue;
   const bool rss = mode == SegMode::kRssOnly;
   if (vals) {
     return rss ? launch_sort<K, true, true>(keys, vals, offsets, nseg, scratch, t, s, d)
