@@ -180,7 +180,7 @@ def part_bytes(inp):
     return {"sweep": sweep, "uneven": uneven, "rss": rss}
 
 
-LAUNCHES_PER_STEP = len(SWEEP_NS) + 2 + 2
+LAUNCHES_PER_STEP = len(SWEEP_NS) + 4 + 4  # fixed-n launches + (plan, bin, tile, rss) x 2
 
 
 PARTS = ("sweep", "uneven", "rss")

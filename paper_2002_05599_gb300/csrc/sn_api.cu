@@ -7,6 +7,7 @@
 #include "smallsort.h"
 #include "sn_common.cuh"
 #include "sn_internal.h"
+#include "sn_seg_scratch.h"
 
 namespace sn {
 
@@ -122,9 +123,7 @@ int segments_entry(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t ns
 namespace sn {
 
 size_t segments_scratch_bytes(uint64_t nseg, const SegTuning& t) {
-  const uint64_t E = static_cast<uint64_t>(t.tile_units);
-  const uint64_t cap = nseg ? (257ull * (nseg - 1)) / E + 2 : 2;
-  return 256 + ((cap * 4 + 255) & ~static_cast<uint64_t>(255));
+  return seg::ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total;
 }
 
 }  // namespace sn
@@ -161,6 +160,14 @@ int rss_sort_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offset
                                   sn::launch_segments_u64);
 }
 
+namespace {
+std::atomic<unsigned> g_last_word{0};
+}
+
+// Raw device status word seen by the latest sn_check (diagnostics; not part
+// of the public interface).
+unsigned sn_debug_status_word(void) { return g_last_word.load(); }
+
 int sn_check(sn_stream_t stream) {
   int err = SN_OK;
   const sn::DeviceInfo* d = sn::device_info(&err);
@@ -171,8 +178,10 @@ int sn_check(sn_stream_t stream) {
   if (cudaMemcpyAsync(&word, d->status, sizeof(word), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SN_ECUDA;
   if (sn::clear_status(*d, s) != cudaSuccess) return SN_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return SN_ECUDA;
+  g_last_word.store(word);
   if (word & sn::kStatusRange) return SN_ERANGE;
   if (word & sn::kStatusTimeout) return SN_ETIMEOUT;
+  if (word & (sn::kStatusInternal | sn::kCheckStageMoved | sn::kCheckCopyArgs | sn::kCheckSegment)) return SN_ECUDA;
   return SN_OK;
 }
 

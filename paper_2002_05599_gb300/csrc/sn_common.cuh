@@ -17,6 +17,11 @@ namespace sn {
 // ---- status bits written by kernels into the per-device status word ----
 constexpr unsigned kStatusRange = 1u;    // bad offsets / segment too long
 constexpr unsigned kStatusTimeout = 2u;  // a bounded wait ran out
+constexpr unsigned kStatusInternal = 4u; // an internal consistency check failed
+// finer internal-check bits (reported together as an internal failure)
+constexpr unsigned kCheckStageMoved = 8u;    // a tile's metadata changed while a work item was in flight
+constexpr unsigned kCheckCopyArgs = 16u;     // a bulk copy's range or alignment was invalid
+constexpr unsigned kCheckSegment = 32u;      // a segment's staged span left its buffer
 
 // Bounded mbarrier waits: a wait gives up after kWaitLimitNs of global time
 // (about two seconds) and reports failure instead of spinning forever.
@@ -180,6 +185,35 @@ __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// CTA-scope release store / acquire load / acq_rel add on shared memory.
+__device__ __forceinline__ void st_release_smem(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_smem(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t atom_add_acq_rel_smem(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(p)), "r"(v)
+               : "memory");
+  return old;
 }
 
 // Wait for the phase with the given parity to complete; false once

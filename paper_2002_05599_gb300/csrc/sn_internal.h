@@ -26,7 +26,7 @@ cudaError_t launch_fixed_u64(uint64_t* keys, int n, uint64_t count, cudaStream_t
 enum class SegMode : int { kNetworkWarpRss = 0, kRssOnly = 1 };
 
 struct SegTuning {
-  int tile_units = 4096;  // segments + elements per tile (512..8192)
+  int tile_units = 2048;  // segments + elements per tile (512..8192)
 };
 
 // Device scratch needed for a segmented call with nseg segments.

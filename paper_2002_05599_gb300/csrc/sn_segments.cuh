@@ -1,84 +1,80 @@
 // Segmented sorting: CSR segments of 0..256 items, keys (u32 / u64) with an
-// optional u32 payload, in one persistent launch.
+// optional u32 payload.  Four stream-ordered launches:
 //
-// Plan (seg_plan_kernel): the batch is cut into tiles.  Segment s gets the
-// position u_s = s + (offsets[s] - offsets[0]) and belongs to tile u_s / E,
-// so a tile holds at most E segments and at most E + 256 items.  The kernel
-// validates every segment and records the first segment of each tile.
-//
-// Sort (seg_sort_kernel, one CTA per SM): one producer warp moves whole tiles
-// (offsets, keys, payload) into shared memory with 1-D bulk copies on a
-// two-stage mbarrier ring.  Sixteen consumer warps bin the tile's segments by
-// length -- the paper's suggestion (Sec. 5) of bucketing base cases by size and
-// solving batches of identical size -- and take work items from a shared
-// counter, largest first:
-//   * 33..256 items (17..256 in RSS-only mode): Register Sample Sort by one
-//     warp (Sec. 3): a sample of 2k items sorted by a network, k-1 splitters
-//     taken equidistant, every item classified by the branch-free descent
-//     j <- 2j + [t_j < e] over the splitter tree (Algorithm 1 generalised), a
-//     stable counting scatter in shared memory, and one network per bucket;
-//   * 17..32 items: the 32-lane warp network, one item per lane;
-//   * 2..16 items: 32 segments of one size class at a time, one per lane, each
-//     sorted in registers by the class's network (2, 4, 8, 12 or 16 channels,
-//     shorter segments padded with +inf).
-// Few distinct networks keep the instruction working set small: with one
-// network per n, warps running different n thrashed the instruction cache
-// (the GPU analogue of the L1i misses the paper measured in Sec. 4.4 / 4.6).
+// 1. seg_plan_kernel -- cuts the batch into tiles.  Segment s gets the
+//    position u_s = s + (offsets[s] - offsets[0]) and belongs to tile u_s / E,
+//    so a tile holds at most E segments and at most E + 256 items.  Every
+//    segment is validated here; bad offsets stop the call before any data is
+//    touched.
+// 2. seg_bin_kernel -- bins every tile's segments by length: the paper's
+//    suggestion (Sec. 5) of bucketing base cases by size so that batches of
+//    identical size are solved together.  Each tile gets class counts and an
+//    index list grouped by class; segments for Register Sample Sort (33+
+//    items, 17+ in RSS-only mode) come last in the list.
+// 3. seg_tile_kernel -- persistent, tiles assigned round-robin (no shared
+//    counter); a producer warp reads the metadata of 32 tiles at a time,
+//    skips tiles with nothing to do and stages the others
+//    (offsets, keys, payload, bins) in shared memory with 1-D bulk copies on
+//    a two-stage mbarrier ring, eight consumer warps take work items:
+//      * 2..16 items: 32 segments per item, one per lane, each sorted in
+//        registers by the network of Sec. 2 for its class (2, 4, 8, 12 or 16
+//        channels, shorter segments padded with +inf);
+//      * 17..32 items: 16 segments per item, two lanes per segment: each
+//        lane sorts 16 items with the 16-channel network, then the lane pair
+//        merges through shuffles (mirrored exchange + in-register half
+//        cleaners), i.e. a 32-item bitonic merge across two lanes.
+//    Sorted tiles return through bulk stores; the partial 16-byte granules at
+//    a tile's ends, shared with its neighbours, are written with plain stores.
+// 4. seg_rss_kernel -- persistent independent warps, tiles assigned
+//    round-robin to warps; each warp walks the RSS entries of its tiles and
+//    prefetches its next segment with a bulk copy while it sorts the
+//    current one by Register Sample Sort (Sec. 3): a sample of 2k items sorted
+//    by a network, k-1 splitters taken equidistant, the branch-free descent
+//    j <- 2j + [t_j < e] over the splitter tree (Algorithm 1 generalised), a
+//    stable counting scatter, and a network per bucket.
 // With a payload, items are (key, position) pairs so ties keep input order and
-// the payload is gathered by position at the end.  Sorted tiles go back with
-// bulk stores; the partial 16-byte granules at a tile's two ends, which it
-// shares with its neighbours, are written with plain stores.
+// the payload is gathered by position at the end.  Few distinct network sizes
+// keep the instruction working set small: with one network per n, warps
+// running different n thrashed the instruction cache (the GPU analogue of the
+// L1i misses the paper measured in Sec. 4.4 / 4.6).
 #pragma once
 
 #include <algorithm>
-#include <atomic>
 
 #include "sn_common.cuh"
 #include "sn_internal.h"
+#include "sn_seg_scratch.h"
 
 namespace sn {
 namespace seg {
 namespace {  // internal linkage: each instantiation unit gets its own copy
 
-constexpr int kConsumerWarps = 16;
-constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kThreads = kConsumers + 32;  // + one producer warp
+constexpr int kTileWarps = 8;
+constexpr int kTileConsumers = kTileWarps * 32;
+constexpr int kTileThreads = kTileConsumers + 32;  // + one producer warp
 constexpr int kStages = 2;
+constexpr int kRssWarps = 8;
+constexpr int kRssThreads = kRssWarps * 32;
 constexpr int kMaxSeg = 256;
 constexpr uint32_t kDone = 0xFFFFFFFFu;
-constexpr int kConsumerBar = 1;  // named barrier id for the consumer warps
 constexpr int kRssMaxBuckets = 64;
+constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Size classes of a tile, in the order their work items are handed out.
-enum Cls : int {
-  kRss64 = 0, kRss32, kRss16, kRss8,  // Register Sample Sort with k buckets
-  kWarp,                              // 17..32 items, warp network
-  kNet16, kNet12, kNet8, kNet4, kNet2,
-  kNumCls,
-  kSkip = kNumCls                     // 0 or 1 item
-};
+// Classes handled by the tile kernel, in list and hand-out order.
+enum TileCls : int { kPair = 0, kNet16, kNet12, kNet8, kNet4, kNet2, kNumTileCls };
+constexpr int kRssCls = kNumTileCls;
+constexpr int kSkipCls = kNumTileCls + 1;
 
 __device__ __forceinline__ int seg_class(uint32_t len, bool rss_only) {
-  if (len <= 1) return kSkip;
+  if (len <= 1) return kSkipCls;
   if (len == 2) return kNet2;
   if (len <= 4) return kNet4;
   if (len <= 8) return kNet8;
   if (len <= 12) return kNet12;
   if (len <= 16) return kNet16;
-  if (len <= 32) return rss_only ? kRss8 : kWarp;
-  if (len <= 64) return kRss16;
-  if (len <= 128) return kRss32;
-  return kRss64;
+  if (len <= 32 && !rss_only) return kPair;
+  return kRssCls;
 }
-
-__device__ __forceinline__ bool cls_is_net(int c) { return c >= kNet16; }
-
-struct Plan {
-  unsigned bad;        // offsets failed validation
-  unsigned next_tile;  // dynamic tile counter
-  unsigned ntiles;
-  unsigned pad;
-};
 
 struct TileMeta {
   uint32_t tile;
@@ -87,53 +83,47 @@ struct TileMeta {
   uint32_t off_shift;     // index of offsets[s0] in the staged offsets
   uint32_t key_shift;     // index of keys[e0] in the staged keys
   uint32_t val_shift;     // index of vals[e0] in the staged payload
+  uint32_t ord_shift;     // index of order[s0] in the staged bins
 };
 
-// ------------------------------------------------------------ layout -------
+// ------------------------------------------------------ staging layouts ----
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
+__host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~static_cast<size_t>(127); }
 
 template <class K, bool kVals>
-struct Layout {
-  uint32_t E;
-  uint32_t off_cap, key_cap, val_cap;  // staged elements per stage
-  size_t off_at, key_at, val_at, stage_bytes;
-  size_t list_at, rss_at, total;
-
-  __host__ __device__ explicit Layout(uint32_t tile_units) : E(tile_units) {
-    off_cap = E + 1 + 8;
-    key_cap = E + kMaxSeg + 2 * (16 / sizeof(K));
-    val_cap = kVals ? E + kMaxSeg + 8 : 0;
+struct TileLayout {
+  size_t off_at, key_at, val_at, ord_at, cnt_at, stage_bytes, total;
+  __host__ __device__ explicit TileLayout(uint32_t E) {
     off_at = 0;
-    key_at = align16(off_at + off_cap * 4);
-    val_at = align16(key_at + static_cast<size_t>(key_cap) * sizeof(K));
-    stage_bytes = align128(val_at + val_cap * 4);
-    list_at = kStages * stage_bytes;
-    rss_at = align128(list_at + static_cast<size_t>(E) * 2);
-    total = rss_at + kConsumerWarps * rss_bytes();
-  }
-  __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
-  __host__ __device__ static size_t align128(size_t x) { return (x + 127) & ~static_cast<size_t>(127); }
-  // per-warp Register Sample Sort scratch: 256 items + 64 bucket counters
-  __host__ __device__ static size_t rss_bytes() {
-    return sizeof(K) == 4 ? 256 * 8 + kRssMaxBuckets * 4 : 256 * 8 + 256 * 2 + kRssMaxBuckets * 4;
+    key_at = align16(off_at + (E + 1 + 8) * 4);
+    val_at = align16(key_at + static_cast<size_t>(E + kMaxSeg + 2 * (16 / sizeof(K))) * sizeof(K));
+    ord_at = align16(val_at + (kVals ? (E + kMaxSeg + 8) * 4 : 0));
+    cnt_at = align16(ord_at + (E + 16) * 2);
+    stage_bytes = align128(cnt_at + 16);
+    total = kStages * stage_bytes;
   }
 };
 
-// Per-warp RSS scratch.  The item buffer also holds the sorted sample (slots
-// 0..S-1) and then the splitter tree (slots S..S+k-1) before the scatter
-// overwrites it: classification finishes before the first scatter store.
+// Per-warp Register Sample Sort scratch: 256 items + 64 bucket counters.  The
+// item buffer also holds the sorted sample (slots 0..S-1) and the splitter
+// tree (slots S..S+k-1) until the scatter overwrites it, which happens only
+// after every item is classified.
 template <class K> struct RssMem;
 template <> struct RssMem<uint32_t> {
-  uint64_t* buf;  // 256 packed items
-  uint32_t* cnt;  // 64 bucket counters
+  static constexpr size_t kBytes = 256 * 8 + kRssMaxBuckets * 4;
+  uint64_t* buf;  // packed (key, position) items
+  uint32_t* cnt;
   __device__ __forceinline__ explicit RssMem(unsigned char* p)
       : buf(reinterpret_cast<uint64_t*>(p)), cnt(reinterpret_cast<uint32_t*>(p + 256 * 8)) {}
   __device__ __forceinline__ uint64_t get(int i) const { return buf[i]; }
   __device__ __forceinline__ void set(int i, uint64_t v) const { buf[i] = v; }
 };
 template <> struct RssMem<uint64_t> {
-  uint64_t* key;  // 256
-  uint16_t* idx;  // 256
-  uint32_t* cnt;  // 64
+  static constexpr size_t kBytes = 256 * 8 + 256 * 2 + kRssMaxBuckets * 4;
+  uint64_t* key;
+  uint16_t* idx;
+  uint32_t* cnt;
   __device__ __forceinline__ explicit RssMem(unsigned char* p)
       : key(reinterpret_cast<uint64_t*>(p)), idx(reinterpret_cast<uint16_t*>(p + 256 * 8)),
         cnt(reinterpret_cast<uint32_t*>(p + 256 * 10)) {}
@@ -142,6 +132,19 @@ template <> struct RssMem<uint64_t> {
     key[i] = v.key;
     idx[i] = static_cast<uint16_t>(v.idx);
   }
+};
+
+// Per-warp region of the RSS kernel: two staging buffers (keys, payload),
+// two mbarriers, the RSS scratch.
+template <class K, bool kVals>
+struct RssWarpLayout {
+  static constexpr size_t kKeyCap = (kMaxSeg + 2 * (16 / sizeof(K))) * sizeof(K);
+  static constexpr size_t kValCap = kVals ? (kMaxSeg + 8) * 4 : 0;
+  static constexpr size_t kBar = 0;
+  static constexpr size_t kKeys = 16;
+  static constexpr size_t kVals_ = kKeys + 2 * kKeyCap;
+  static constexpr size_t kScratch = (kVals_ + 2 * kValCap + 15) & ~static_cast<size_t>(15);
+  static constexpr size_t kBytes = (kScratch + RssMem<K>::kBytes + 127) & ~static_cast<size_t>(127);
 };
 
 // ---------------------------------------------------------------- plan -----
@@ -179,6 +182,54 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ----------------------------------------------------------------- bin -----
+
+// One warp per tile (grid-stride over warps): counts[8t + c] for the tile
+// classes c and counts[8t + 6] for Register Sample Sort, and the tile-local
+// indices of its segments grouped by class in order[s0 .. s1).  Counts live
+// in registers (warp-uniform); positions come from ballots.
+__global__ void __launch_bounds__(256)
+    seg_bin_kernel(const uint32_t* __restrict__ offsets, const Plan* plan, const uint32_t* __restrict__ tile_first,
+                   uint16_t* __restrict__ counts, uint16_t* __restrict__ order, bool rss_only) {
+  constexpr int kCls = kNumTileCls + 1;  // tile classes + RSS
+  const int lane = threadIdx.x & 31;
+  const unsigned ntiles = plan->bad ? 0u : plan->ntiles;
+  const unsigned W = gridDim.x * (blockDim.x / 32);
+  const unsigned lt = (1u << lane) - 1u;
+  for (unsigned t = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); t < ntiles; t += W) {
+    const uint32_t s0 = tile_first[t], s1 = tile_first[t + 1];
+    const uint32_t ns = s1 - s0;
+    uint32_t cnt[kCls];
+#pragma unroll
+    for (int q = 0; q < kCls; ++q) cnt[q] = 0;
+    for (uint32_t i0 = 0; i0 < ns; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const int c = i < ns ? seg_class(offsets[s0 + i + 1] - offsets[s0 + i], rss_only) : kSkipCls;
+#pragma unroll
+      for (int q = 0; q < kCls; ++q) cnt[q] += __popc(__ballot_sync(kFull, c == q));
+    }
+    uint32_t cur[kCls];
+    uint32_t at = 0;
+#pragma unroll
+    for (int q = 0; q < kCls; ++q) {
+      cur[q] = at;
+      at += cnt[q];
+      if (lane == q) counts[8ull * t + q] = static_cast<uint16_t>(cnt[q]);
+    }
+    if (lane == 7) counts[8ull * t + 7] = 0;
+    for (uint32_t i0 = 0; i0 < ns; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const int c = i < ns ? seg_class(offsets[s0 + i + 1] - offsets[s0 + i], rss_only) : kSkipCls;
+#pragma unroll
+      for (int q = 0; q < kCls; ++q) {
+        const unsigned m = __ballot_sync(kFull, c == q);
+        if (c == q) order[s0 + cur[q] + __popc(m & lt)] = static_cast<uint16_t>(i);
+        cur[q] += __popc(m);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------ per-lane networks --
 
 // Segment of L <= N items at kbuf[p..p+L), padded with +inf to N channels
@@ -213,26 +264,85 @@ __device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int 
   }
 }
 
-// ------------------------------------------------------- warp network ------
+// ---------------------------------------------------- 17..32 on two lanes --
 
+template <class T>
+__device__ __forceinline__ T lo_of(const T& a, const T& b) {
+  return item_less(b, a) ? b : a;
+}
+template <class T>
+__device__ __forceinline__ T hi_of(const T& a, const T& b) {
+  return item_less(b, a) ? a : b;
+}
+__device__ __forceinline__ uint32_t lo_of(uint32_t a, uint32_t b) { return min(a, b); }
+__device__ __forceinline__ uint32_t hi_of(uint32_t a, uint32_t b) { return max(a, b); }
+__device__ __forceinline__ uint64_t lo_of(uint64_t a, uint64_t b) { return min(a, b); }
+__device__ __forceinline__ uint64_t hi_of(uint64_t a, uint64_t b) { return max(a, b); }
+
+// 32 channels on a lane pair: the even lane holds items 0..15, the odd lane
+// 16..31; both sort with the 16-channel network, then a bitonic merge: the
+// mirrored exchange x_i <-> partner x_{15-i} leaves the 16 smallest on the
+// even lane and the 16 largest on the odd lane, each a bitonic sequence that
+// four in-register half-cleaner levels sort.
+template <class T>
+__device__ __forceinline__ void pair_network32(T (&x)[16], bool upper) {
+  Net<16>::run(x);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const T a = shfl_xor(x[15 - q], 1);
+    const T b = shfl_xor(x[q], 1);
+    if (upper) {
+      x[q] = hi_of(x[q], a);
+      x[15 - q] = hi_of(x[15 - q], b);
+    } else {
+      x[q] = lo_of(x[q], a);
+      x[15 - q] = lo_of(x[15 - q], b);
+    }
+  }
+#pragma unroll
+  for (int m = 8; m >= 1; m >>= 1) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if ((i & m) == 0) ce(x[i], x[i | m]);
+  }
+}
+
+// Segment of 17..32 items handled by lanes (lane & ~1, lane | 1).  Lanes whose
+// pair has no segment (active = false) still take part in the shuffles.
 template <class K, bool kVals>
-__device__ __forceinline__ void warp_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, int lane) {
+__device__ __forceinline__ void pair_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, bool active,
+                                             int lane) {
+  const bool upper = lane & 1;
+  const int base = upper ? 16 : 0;
   if constexpr (kVals) {
     using IO = ItemOf<K>;
-    typename IO::T x = lane < L ? IO::make(kbuf[p + lane], lane) : IO::sentinel(lane);
-    warp_network32(x, lane);
-    uint32_t v = 0;
-    if (lane < L) v = vbuf[pv + IO::idx(x)];
+    typename IO::T x[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      x[q] = (active && base + q < L) ? IO::make(kbuf[p + base + q], base + q) : IO::sentinel(base + q);
+    pair_network32(x, upper);
+    uint32_t v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (active && base + q < L) v[q] = vbuf[pv + IO::idx(x[q])];
     __syncwarp();
-    if (lane < L) {
-      kbuf[p + lane] = IO::key(x);
-      vbuf[pv + lane] = v;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      if (active && base + q < L) {
+        kbuf[p + base + q] = IO::key(x[q]);
+        vbuf[pv + base + q] = v[q];
+      }
     }
   } else {
-    K x = lane < L ? kbuf[p + lane] : static_cast<K>(~static_cast<K>(0));
-    warp_network32(x, lane);
+    K x[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      x[q] = (active && base + q < L) ? kbuf[p + base + q] : static_cast<K>(~static_cast<K>(0));
+    pair_network32(x, upper);
     __syncwarp();
-    if (lane < L) kbuf[p + lane] = x;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (active && base + q < L) kbuf[p + base + q] = x[q];
   }
 }
 
@@ -318,7 +428,6 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
                                             int lane) {
   using IO = ItemOf<K>;
   using It = typename IO::T;
-  const unsigned kFull = 0xFFFFFFFFu;
 
   // k buckets with at most L/4 expected items each (k in 8..64), sample of 2k
   int B = 8;
@@ -464,35 +573,66 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
   __syncwarp();
 }
 
-// ------------------------------------------------------------ main kernel --
+// ------------------------------------------------- staged range stores -----
 
-__device__ __forceinline__ bool consumers_or(bool pred) {
-  uint32_t out;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, %2, %3, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(out)
-      : "r"(pred ? 1u : 0u), "n"(kConsumerBar), "n"(kConsumers)
-      : "memory");
-  return out != 0;
+// Write items [e0, e0 + n) from the staged copy (granule-aligned, element
+// e0 at index shift) back to `dst`: bulk store for the whole 16-byte granules
+// (issued by lane 0 into the current bulk group), plain stores by the calling
+// warp's lanes for the partial granules at both ends.
+template <class T>
+__device__ __forceinline__ void store_range(T* dst, const T* staged, uint32_t shift, uint32_t e0, uint32_t n,
+                                            int lane) {
+  if (n == 0) return;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(dst + e0), z = reinterpret_cast<uintptr_t>(dst + e0 + n);
+  const uintptr_t ia = (a + 15) & ~uintptr_t(15), iz = z & ~uintptr_t(15);
+  uint32_t head = n, tail = n;
+  if (ia < iz) {
+    head = static_cast<uint32_t>((ia - a) / sizeof(T));
+    tail = static_cast<uint32_t>((iz - a) / sizeof(T));
+    if (lane == 0) bulk_s2g(reinterpret_cast<void*>(ia), staged + shift + head, static_cast<uint32_t>(iz - ia));
+  }
+  for (uint32_t e = lane; e < head; e += 32) dst[e0 + e] = staged[shift + e];
+  for (uint32_t e = tail + lane; e < n; e += 32) dst[e0 + e] = staged[shift + e];
 }
 
-template <class K, bool kVals, bool kRssOnly>
-__global__ void __launch_bounds__(kThreads, 1)
-    seg_sort_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
-                    const Plan* plan_c, Plan* plan, const uint32_t* __restrict__ tile_first, uint32_t E,
-                    unsigned* status) {
-  using L_ = Layout<K, kVals>;
-  const L_ lay(E);
+// ----------------------------------------------------------- tile kernel ---
+
+constexpr int kRing = 256;  // task ring slots (>= 2 tiles of tasks + sentinels)
+constexpr uint32_t kRingDone = 0xFFFFFFFFu;
+
+struct TileTasks {
+  uint32_t npair, pair_tasks, ntasks, b16, b12, b8, b4, b2;
+};
+
+// Work items of a staged tile: 16 pair segments per item, then the network
+// list (classes 16, 12, 8, 4, 2 in that order) in chunks of 32 lanes; a chunk
+// that spans two classes uses the larger network for all its lanes.
+__device__ __forceinline__ TileTasks tile_tasks(const uint16_t* cnt) {
+  TileTasks t;
+  t.npair = cnt[kPair];
+  t.b16 = t.npair + cnt[kNet16];
+  t.b12 = t.b16 + cnt[kNet12];
+  t.b8 = t.b12 + cnt[kNet8];
+  t.b4 = t.b8 + cnt[kNet4];
+  t.b2 = t.b4 + cnt[kNet2];
+  t.pair_tasks = (t.npair + 15) / 16;
+  t.ntasks = t.pair_tasks + (t.b2 - t.npair + 31) / 32;
+  return t;
+}
+
+template <class K, bool kVals>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    seg_tile_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
+                    const Plan* plan, const uint32_t* __restrict__ tile_first, const uint16_t* __restrict__ counts,
+                    const uint16_t* __restrict__ order, uint32_t E, unsigned* status) {
+  const TileLayout<K, kVals> lay(E);
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
   __shared__ TileMeta meta[kStages];
-  __shared__ uint32_t cls_cnt[kNumCls], cls_base[kNumCls], cls_cur[kNumCls];
-  __shared__ uint32_t task_base[kNumCls + 1];
-  __shared__ uint32_t task_ctr;
+  __shared__ uint32_t ntasks_of[kStages], done_ctr[kStages];
+  __shared__ uint32_t ring[kRing];
+  __shared__ uint32_t ring_head, ring_tail;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -502,277 +642,490 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      done_ctr[s] = 0;
     }
+    ring_head = 0;
+    ring_tail = 0;
     fence_mbar_init();
   }
-  if (tid < kNumCls) cls_cnt[tid] = 0;
-  if (tid == 0) task_ctr = 0;
   __syncthreads();
 
   // ------------------------------------------------------------ producer --
-  if (warp == kConsumerWarps) {
-    if (lane == 0) {
-      const uint32_t ntiles = plan_c->bad ? 0u : plan_c->ntiles;
-      const uintptr_t kb = reinterpret_cast<uintptr_t>(keys);
-      const uintptr_t vb = reinterpret_cast<uintptr_t>(vals);
-      const uintptr_t ob = reinterpret_cast<uintptr_t>(offsets);
-      for (uint32_t k = 0;; ++k) {
-        const int s = k & 1;
-        if (k >= kStages && !mbar_wait(&empty[s], ((k >> 1) - 1) & 1u)) {
-          atomicOr(status, kStatusTimeout);
-          break;
+  // Tiles blockIdx.x + j * gridDim.x, j = 0, 1, ...; lane i reads the
+  // metadata of tile j = 32 m + i.  The warp stages tiles into the two stages
+  // as they free up and, as each staged copy lands, pushes the tile's work
+  // items onto the ring.
+  if (warp == kTileWarps) {
+    const uint32_t ntiles = plan->bad ? 0u : plan->ntiles;
+    const uintptr_t kb = reinterpret_cast<uintptr_t>(keys);
+    const uintptr_t vb = reinterpret_cast<uintptr_t>(vals);
+    const uintptr_t ob = reinterpret_cast<uintptr_t>(offsets);
+    const uintptr_t rb = reinterpret_cast<uintptr_t>(order);
+    uint32_t chunk = blockIdx.x;
+    bool more = chunk < ntiles;
+    unsigned avail = 0;
+    uint32_t t = 0, s0 = 0, s1 = 0, e0 = 0, e1 = 0;
+    uint32_t issued = 0, pushed = 0, tail = 0;
+    bool failed = false;
+    unsigned long long idle_since = 0;
+    for (;;) {
+      if (avail == 0 && more) {
+        t = chunk + lane * gridDim.x;
+        bool has = false;
+        if (t < ntiles) {
+          const uint2 c03 = *reinterpret_cast<const uint2*>(counts + 8ull * t);
+          const uint32_t c45 = *reinterpret_cast<const uint32_t*>(counts + 8ull * t + 4);
+          has = (c03.x | c03.y | c45) != 0;
+          if (has) {
+            s0 = tile_first[t];
+            s1 = tile_first[t + 1];
+            e0 = offsets[s0];
+            e1 = offsets[s1];
+          }
         }
-        const uint32_t t = atomicAdd(&plan->next_tile, 1u);
-        TileMeta& m = meta[s];
-        if (t >= ntiles) {
-          m.tile = kDone;
-          mbar_arrive(&full[s]);
-          break;
-        }
-        const uint32_t s0 = tile_first[t], s1 = tile_first[t + 1];
-        const uint32_t e0 = offsets[s0], e1 = offsets[s1];
-        unsigned char* stage = smem + s * lay.stage_bytes;
-        // granule-rounded source ranges (a 16-byte granule never crosses a
-        // page, so reading its unused part cannot fault; it is discarded)
-        const uintptr_t oa = (ob + 4ull * s0) & ~uintptr_t(15);
-        const uintptr_t oz = (ob + 4ull * (s1 + 1) + 15) & ~uintptr_t(15);
-        const uintptr_t ka = (kb + sizeof(K) * e0) & ~uintptr_t(15);
-        const uintptr_t kz = (kb + sizeof(K) * e1 + 15) & ~uintptr_t(15);
-        uint32_t bytes = static_cast<uint32_t>(oz - oa);
-        m.tile = t;
-        m.s0 = s0;
-        m.s1 = s1;
-        m.e0 = e0;
-        m.e1 = e1;
-        m.off_shift = static_cast<uint32_t>((ob + 4ull * s0 - oa) / 4);
-        m.key_shift = static_cast<uint32_t>((kb + sizeof(K) * e0 - ka) / sizeof(K));
-        const bool has_items = e1 > e0;
-        if (has_items) bytes += static_cast<uint32_t>(kz - ka);
-        uintptr_t va = 0, vz = 0;
-        if constexpr (kVals) {
-          va = (vb + 4ull * e0) & ~uintptr_t(15);
-          vz = (vb + 4ull * e1 + 15) & ~uintptr_t(15);
-          m.val_shift = static_cast<uint32_t>((vb + 4ull * e0 - va) / 4);
-          if (has_items) bytes += static_cast<uint32_t>(vz - va);
-        } else {
-          m.val_shift = 0;
-        }
-        mbar_arrive_expect_tx(&full[s], bytes);
-        bulk_g2s(stage + lay.off_at, reinterpret_cast<const void*>(oa), static_cast<uint32_t>(oz - oa), &full[s]);
-        if (has_items) {
-          bulk_g2s(stage + lay.key_at, reinterpret_cast<const void*>(ka), static_cast<uint32_t>(kz - ka), &full[s]);
-          if constexpr (kVals)
-            bulk_g2s(stage + lay.val_at, reinterpret_cast<const void*>(va), static_cast<uint32_t>(vz - va),
+        avail = __ballot_sync(kFull, has);
+        chunk += 32u * gridDim.x;
+        more = chunk < ntiles;
+        continue;
+      }
+      if (avail == 0 && !more && pushed == issued) break;
+      bool progress = false;
+      // stage the next tile when its stage is free (lane 0 tests, all lanes follow)
+      bool can_issue = false;
+      if (lane == 0)
+        can_issue = avail != 0 && (issued < kStages || mbar_test(&empty[issued & 1], ((issued >> 1) - 1) & 1u));
+      can_issue = __shfl_sync(kFull, can_issue, 0);
+      if (can_issue) {
+        const int j = __ffs(avail) - 1;
+        avail &= avail - 1;
+        const uint32_t tj = __shfl_sync(kFull, t, j), s0j = __shfl_sync(kFull, s0, j),
+                       s1j = __shfl_sync(kFull, s1, j), e0j = __shfl_sync(kFull, e0, j),
+                       e1j = __shfl_sync(kFull, e1, j);
+        bool staged = true;
+        if (lane == 0) {
+          const int s = issued & 1;
+          unsigned char* stage = smem + s * lay.stage_bytes;
+          // granule-rounded source ranges (a 16-byte granule never crosses a
+          // page, so reading its unused part cannot fault; it is discarded)
+          const uintptr_t oa = (ob + 4ull * s0j) & ~uintptr_t(15);
+          const uintptr_t oz = (ob + 4ull * (s1j + 1) + 15) & ~uintptr_t(15);
+          const uintptr_t ra = (rb + 2ull * s0j) & ~uintptr_t(15);
+          const uintptr_t rz = (rb + 2ull * s1j + 15) & ~uintptr_t(15);
+          const uintptr_t ka = (kb + sizeof(K) * e0j) & ~uintptr_t(15);
+          const uintptr_t kz = (kb + sizeof(K) * e1j + 15) & ~uintptr_t(15);
+          TileMeta& m = meta[s];
+          m.tile = tj;
+          m.s0 = s0j;
+          m.s1 = s1j;
+          m.e0 = e0j;
+          m.e1 = e1j;
+          m.off_shift = static_cast<uint32_t>((ob + 4ull * s0j - oa) / 4);
+          m.ord_shift = static_cast<uint32_t>((rb + 2ull * s0j - ra) / 2);
+          m.key_shift = static_cast<uint32_t>((kb + sizeof(K) * e0j - ka) / sizeof(K));
+          uint32_t bytes = static_cast<uint32_t>((oz - oa) + (rz - ra) + 16);
+          const bool has_items = e1j > e0j;
+          if (has_items) bytes += static_cast<uint32_t>(kz - ka);
+          uintptr_t va = 0, vz = 0;
+          if constexpr (kVals) {
+            va = (vb + 4ull * e0j) & ~uintptr_t(15);
+            vz = (vb + 4ull * e1j + 15) & ~uintptr_t(15);
+            m.val_shift = static_cast<uint32_t>((vb + 4ull * e0j - va) / 4);
+            if (has_items) bytes += static_cast<uint32_t>(vz - va);
+          } else {
+            m.val_shift = 0;
+          }
+          // self-check of every copy's range against its staging buffer
+          const bool args_ok = s1j > s0j && s1j - s0j <= E && e1j >= e0j && e1j - e0j <= E + kMaxSeg &&
+                               (oz - oa) <= lay.key_at - lay.off_at && (rz - ra) <= lay.cnt_at - lay.ord_at &&
+                               (!has_items || (kz - ka) <= lay.val_at - lay.key_at) &&
+                               (!kVals || !has_items || (vz - va) <= lay.ord_at - lay.val_at) &&
+                               ((reinterpret_cast<uintptr_t>(counts) + 16ull * tj) & 15) == 0;
+          if (!args_ok) {
+            atomicOr(status, kStatusInternal | kCheckCopyArgs);
+            staged = false;  // skip the tile; its data stays untouched
+          } else {
+          mbar_arrive_expect_tx(&full[s], bytes);
+          bulk_g2s(stage + lay.off_at, reinterpret_cast<const void*>(oa), static_cast<uint32_t>(oz - oa), &full[s]);
+          bulk_g2s(stage + lay.ord_at, reinterpret_cast<const void*>(ra), static_cast<uint32_t>(rz - ra), &full[s]);
+          bulk_g2s(stage + lay.cnt_at, counts + 8ull * tj, 16, &full[s]);
+          if (has_items) {
+            bulk_g2s(stage + lay.key_at, reinterpret_cast<const void*>(ka), static_cast<uint32_t>(kz - ka),
                      &full[s]);
+            if constexpr (kVals)
+              bulk_g2s(stage + lay.val_at, reinterpret_cast<const void*>(va), static_cast<uint32_t>(vz - va),
+                       &full[s]);
+          }
+          }
         }
+        staged = __shfl_sync(kFull, staged, 0);
+        if (staged) ++issued;
+        progress = true;
+      }
+      // publish the work items of the oldest staged tile once it has landed
+      bool can_push = false;
+      if (lane == 0) can_push = pushed < issued && mbar_test(&full[pushed & 1], (pushed >> 1) & 1u);
+      can_push = __shfl_sync(kFull, can_push, 0);
+      if (can_push) {
+        const int s = pushed & 1;
+        // only lane 0 observed the copy's completion, so only lane 0 reads the
+        // staged counts; the task count is broadcast
+        uint32_t ntasks = 0;
+        if (lane == 0)
+          ntasks = tile_tasks(reinterpret_cast<const uint16_t*>(smem + s * lay.stage_bytes + lay.cnt_at)).ntasks;
+        ntasks = __shfl_sync(kFull, ntasks, 0);
+        const TileTasks tt{0, 0, ntasks, 0, 0, 0, 0, 0};
+        // item = stage << 17 | phase parity of this use of the stage << 16 | index
+        const uint32_t tag = (static_cast<uint32_t>(s) << 17) | (((pushed >> 1) & 1u) << 16);
+        for (uint32_t i = lane; i < tt.ntasks; i += 32) ring[(tail + i) & (kRing - 1)] = tag | i;
+        if (lane == 0) ntasks_of[s] = tt.ntasks;
+        __syncwarp();
+        tail += tt.ntasks;
+        if (lane == 0) st_release_smem(&ring_tail, tail);
+        ++pushed;
+        progress = true;
+      }
+      if (progress) {
+        idle_since = 0;
+      } else {
+        const unsigned long long now = global_ns();
+        if (idle_since == 0) idle_since = now;
+        if (now - idle_since > kWaitLimitNs) {
+          failed = true;
+          break;
+        }
+        __nanosleep(64);
       }
     }
+    if (failed && lane == 0) atomicOr(status, kStatusTimeout);
+    // one stop item per consumer warp
+    for (uint32_t i = lane; i < kTileWarps; i += 32) ring[(tail + i) & (kRing - 1)] = kRingDone;
+    __syncwarp();
+    if (lane == 0) st_release_smem(&ring_tail, tail + kTileWarps);
     return;
   }
 
   // ----------------------------------------------------------- consumers --
-  uint16_t* seg_list = reinterpret_cast<uint16_t*>(smem + lay.list_at);
-  const RssMem<K> rm(smem + lay.rss_at + warp * L_::rss_bytes());
-  const unsigned kFull = 0xFFFFFFFFu;
-
-  for (uint32_t k = 0;; ++k) {
-    const int s = k & 1;
-    const bool ok = mbar_wait(&full[s], (k >> 1) & 1u);
-    if (consumers_or(!ok)) {
-      if (tid == 0) atomicOr(status, kStatusTimeout);
+  bool stored = false;
+  for (;;) {
+    uint32_t desc = kRingDone;
+    if (lane == 0) {
+      const uint32_t pos = atomicAdd(&ring_head, 1u);
+      const unsigned long long t0 = global_ns();
+      bool ok = true;
+      while (ld_acquire_smem(&ring_tail) <= pos) {
+        if (global_ns() - t0 > kWaitLimitNs) {
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+      if (ok) {
+        desc = ring[pos & (kRing - 1)];
+      } else {
+        atomicOr(status, kStatusTimeout);
+      }
+    }
+    desc = __shfl_sync(kFull, desc, 0);
+    if (desc == kRingDone) break;
+    const int s = static_cast<int>(desc >> 17);
+    const uint32_t task = desc & 0xFFFFu;
+    if (s >= kStages) {  // a malformed work item: report, never index with it
+      if (lane == 0) atomicOr(status, kStatusInternal);
       break;
     }
-    const TileMeta m = meta[s];
-    if (m.tile == kDone) break;
-
+    // Bulk-copy writes are visible to the threads that observe the mbarrier
+    // phase, so every lane waits on the stage itself (the phase has completed;
+    // the stage cannot move on while this item is outstanding).
+    if (!__all_sync(kFull, mbar_wait(&full[s], (desc >> 16) & 1u))) {
+      if (lane == 0) atomicOr(status, kStatusTimeout);
+      break;
+    }
+    const TileMeta m = meta[s];  // copy: checked against the stage again before the store
     unsigned char* stage = smem + s * lay.stage_bytes;
     const uint32_t* obuf = reinterpret_cast<const uint32_t*>(stage + lay.off_at) + m.off_shift;
+    const uint16_t* ord = reinterpret_cast<const uint16_t*>(stage + lay.ord_at) + m.ord_shift;
     K* kbuf = reinterpret_cast<K*>(stage + lay.key_at);
     uint32_t* vbuf = reinterpret_cast<uint32_t*>(stage + lay.val_at);
-    const int ns = static_cast<int>(m.s1 - m.s0);
-    const int nrounds = (ns + kConsumers - 1) / kConsumers;
+    const TileTasks tt = tile_tasks(reinterpret_cast<const uint16_t*>(stage + lay.cnt_at));
+    const uint32_t e0 = m.e0, key_shift = m.key_shift, val_shift = m.val_shift;
+    const uint32_t ns = m.s1 - m.s0;
+    if (task >= tt.ntasks || tt.b2 > ns || ns > E) {
+      if (lane == 0) atomicOr(status, kStatusInternal);
+      break;
+    }
 
-    // --- bin the tile's segments by size class (warp-aggregated counts)
-    for (int r = 0; r < nrounds; ++r) {
-      const int i = r * kConsumers + tid;
-      const int c = i < ns ? seg_class(obuf[i + 1] - obuf[i], kRssOnly) : kSkip;
-#pragma unroll
-      for (int q = 0; q < kNumCls; ++q) {
-        const unsigned mask = __ballot_sync(kFull, c == q);
-        if (mask && lane == __ffs(mask) - 1) atomicAdd(&cls_cnt[q], __popc(mask));
-      }
-    }
-    named_bar_sync(kConsumerBar, kConsumers);
-    if (tid == 0) {
-      uint32_t at = 0, tasks = 0;
-      for (int q = 0; q < kNumCls; ++q) {
-        cls_base[q] = at;
-        cls_cur[q] = at;
-        at += cls_cnt[q];
-        task_base[q] = tasks;
-        tasks += cls_is_net(q) ? (cls_cnt[q] + 31) / 32 : cls_cnt[q];
-      }
-      task_base[kNumCls] = tasks;
-    }
-    named_bar_sync(kConsumerBar, kConsumers);
-    for (int r = 0; r < nrounds; ++r) {
-      const int i = r * kConsumers + tid;
-      const int c = i < ns ? seg_class(obuf[i + 1] - obuf[i], kRssOnly) : kSkip;
-#pragma unroll
-      for (int q = 0; q < kNumCls; ++q) {
-        const unsigned mask = __ballot_sync(kFull, c == q);
-        if (mask) {
-          uint32_t at = 0;
-          if (lane == __ffs(mask) - 1) at = atomicAdd(&cls_cur[q], __popc(mask));
-          at = __shfl_sync(kFull, at, __ffs(mask) - 1);
-          if (c == q) seg_list[at + __popc(mask & ((1u << lane) - 1u))] = static_cast<uint16_t>(i);
+    // self-check: a segment's staged span must lie inside the stage buffers
+    const uint32_t key_cap = static_cast<uint32_t>((lay.val_at - lay.key_at) / sizeof(K));
+    const uint32_t val_cap = kVals ? static_cast<uint32_t>((lay.ord_at - lay.val_at) / 4) : 0xFFFFFFFFu;
+    auto span_ok = [&](uint32_t i, uint32_t& o, uint32_t& L) -> bool {
+      if (i >= ns) return false;
+      o = obuf[i];
+      const uint32_t o1 = obuf[i + 1];
+      if (o < e0 || o1 < o || o1 > m.e1 || o1 - o > 32) return false;
+      L = o1 - o;
+      return o1 - e0 + key_shift <= key_cap && o1 - e0 + val_shift <= val_cap;
+    };
+    if (task < tt.pair_tasks) {
+      const uint32_t slot = task * 16 + (lane >> 1);
+      bool active = slot < tt.npair;
+      int p = 0, pv = 0, L = 0;
+      if (active) {
+        uint32_t o = 0, l = 0;
+        if (span_ok(ord[slot], o, l)) {
+          L = static_cast<int>(l);
+          p = static_cast<int>(o - e0 + key_shift);
+          pv = static_cast<int>(o - e0 + val_shift);
+        } else {
+          atomicOr(status, kStatusInternal | kCheckSegment);
+          active = false;
         }
       }
-    }
-    named_bar_sync(kConsumerBar, kConsumers);
-
-    // --- work items, largest classes first
-    const uint32_t ntasks = task_base[kNumCls];
-    const uint32_t e0 = m.e0;
-    for (;;) {
-      uint32_t task = 0;
-      if (lane == 0) task = atomicAdd(&task_ctr, 1u);
-      task = __shfl_sync(kFull, task, 0);
-      if (task >= ntasks) break;
-      int q = 0;
-      while (task >= task_base[q + 1]) ++q;
-      const uint32_t j = task - task_base[q];
-      if (!cls_is_net(q)) {
-        const int i = seg_list[cls_base[q] + j];
-        const uint32_t o = obuf[i];
-        const int L = static_cast<int>(obuf[i + 1] - o);
-        const int p = static_cast<int>(o - e0 + m.key_shift);
-        const int pv = static_cast<int>(o - e0 + m.val_shift);
-        if (q == kWarp)
-          warp_segment<K, kVals>(kbuf, vbuf, p, pv, L, lane);
+      pair_segment<K, kVals>(kbuf, vbuf, p, pv, L, active, lane);
+    } else {
+      const uint32_t first = tt.npair + (task - tt.pair_tasks) * 32;
+      const uint32_t slot = first + lane;
+      uint32_t o = 0, l = 0;
+      const bool ok_seg = slot < tt.b2 && span_ok(ord[slot], o, l) && l <= 16;
+      if (slot < tt.b2 && !ok_seg) atomicOr(status, kStatusInternal | kCheckSegment);
+      if (ok_seg) {
+        const int L = static_cast<int>(l);
+        const int p = static_cast<int>(o - e0 + key_shift);
+        const int pv = static_cast<int>(o - e0 + val_shift);
+        if (first < tt.b16)
+          net_segment<16, K, kVals>(kbuf, vbuf, p, pv, L);
+        else if (first < tt.b12)
+          net_segment<12, K, kVals>(kbuf, vbuf, p, pv, L);
+        else if (first < tt.b8)
+          net_segment<8, K, kVals>(kbuf, vbuf, p, pv, L);
+        else if (first < tt.b4)
+          net_segment<4, K, kVals>(kbuf, vbuf, p, pv, L);
         else
-          rss_segment<K, kVals>(kbuf, vbuf, p, pv, L, rm, lane);
-      } else {
-        const uint32_t slot = j * 32 + lane;
-        if (slot < cls_cnt[q]) {
-          const int i = seg_list[cls_base[q] + slot];
-          const uint32_t o = obuf[i];
-          const int L = static_cast<int>(obuf[i + 1] - o);
-          const int p = static_cast<int>(o - e0 + m.key_shift);
-          const int pv = static_cast<int>(o - e0 + m.val_shift);
-          switch (q) {
-            case kNet16: net_segment<16, K, kVals>(kbuf, vbuf, p, pv, L); break;
-            case kNet12: net_segment<12, K, kVals>(kbuf, vbuf, p, pv, L); break;
-            case kNet8: net_segment<8, K, kVals>(kbuf, vbuf, p, pv, L); break;
-            case kNet4: net_segment<4, K, kVals>(kbuf, vbuf, p, pv, L); break;
-            default: net_segment<2, K, kVals>(kbuf, vbuf, p, pv, L); break;
-          }
-        }
+          net_segment<2, K, kVals>(kbuf, vbuf, p, pv, L);
       }
     }
 
-    // --- store the tile; reset the counters for the next one
+    // completion: the warp that finishes a tile's last item stores the tile
+    // and releases its stage
     fence_proxy_async_smem();
-    named_bar_sync(kConsumerBar, kConsumers);
-    if (tid < kNumCls) cls_cnt[tid] = 0;
-    if (tid == 32) task_ctr = 0;
-    if (m.e1 > m.e0) {
-      const uintptr_t kb = reinterpret_cast<uintptr_t>(keys);
-      const uintptr_t a = kb + sizeof(K) * m.e0, z = kb + sizeof(K) * m.e1;
-      const uintptr_t ia = (a + 15) & ~uintptr_t(15), iz = z & ~uintptr_t(15);
-      uintptr_t va = 0, vz = 0, via = 0, viz = 0;
-      if constexpr (kVals) {
-        const uintptr_t vb = reinterpret_cast<uintptr_t>(vals);
-        va = vb + 4ull * m.e0;
-        vz = vb + 4ull * m.e1;
-        via = (va + 15) & ~uintptr_t(15);
-        viz = vz & ~uintptr_t(15);
-      }
-      if (tid == 0) {
-        if (ia < iz)
-          bulk_s2g(reinterpret_cast<void*>(ia), kbuf + m.key_shift + (ia - a) / sizeof(K),
-                   static_cast<uint32_t>(iz - ia));
-        if constexpr (kVals) {
-          if (via < viz)
-            bulk_s2g(reinterpret_cast<void*>(via), vbuf + m.val_shift + (via - va) / 4,
-                     static_cast<uint32_t>(viz - via));
-        }
-        bulk_commit();
-      }
-      // partial granules at both ends: plain stores
-      if (warp == 1) {
-        const uint32_t n_items = m.e1 - m.e0;
-        const uint32_t head = ia < iz ? static_cast<uint32_t>((ia - a) / sizeof(K)) : n_items;
-        const uint32_t tail_from = ia < iz ? static_cast<uint32_t>((iz - a) / sizeof(K)) : n_items;
-        for (uint32_t e = lane; e < head; e += 32) keys[m.e0 + e] = kbuf[m.key_shift + e];
-        for (uint32_t e = tail_from + lane; e < n_items; e += 32) keys[m.e0 + e] = kbuf[m.key_shift + e];
-        if constexpr (kVals) {
-          const uint32_t vhead = via < viz ? static_cast<uint32_t>((via - va) / 4) : n_items;
-          const uint32_t vtail = via < viz ? static_cast<uint32_t>((viz - va) / 4) : n_items;
-          for (uint32_t e = lane; e < vhead; e += 32) vals[m.e0 + e] = vbuf[m.val_shift + e];
-          for (uint32_t e = vtail + lane; e < n_items; e += 32) vals[m.e0 + e] = vbuf[m.val_shift + e];
-        }
-      }
-      if (tid == 0) bulk_wait_read<0>();
+    __syncwarp();
+    uint32_t fin = 0;
+    if (lane == 0) {
+      const uint32_t total = ntasks_of[s];
+      fin = (atom_add_acq_rel_smem(&done_ctr[s], 1u) + 1 == total) ? 1u : 0u;
     }
-    named_bar_sync(kConsumerBar, kConsumers);
-    if (tid == 0) mbar_arrive(&empty[s]);
+    fin = __shfl_sync(kFull, fin, 0);
+    if (fin) {
+      // self-check: the stage must still hold this work item's tile
+      const TileMeta now = meta[s];
+      if (now.tile != m.tile || now.e0 != m.e0 || now.e1 != m.e1 || m.e1 - e0 > E + kMaxSeg) {
+        if (lane == 0) atomicOr(status, kStatusInternal | kCheckStageMoved);
+        break;
+      }
+      store_range<K>(keys, kbuf, key_shift, e0, m.e1 - e0, lane);
+      if constexpr (kVals) store_range<uint32_t>(vals, vbuf, val_shift, e0, m.e1 - e0, lane);
+      stored = true;
+      __syncwarp();  // every lane's reads of the stage are done
+      if (lane == 0) {
+        bulk_commit();
+        bulk_wait_read<0>();
+        done_ctr[s] = 0;
+        mbar_arrive(&empty[s]);
+      }
+      __syncwarp();
+    }
   }
-  if (tid == 0) bulk_wait_all<0>();
+  if (stored && lane == 0) bulk_wait_all<0>();
+}
+
+// ------------------------------------------------------------ RSS kernel ---
+
+// Stage items [e0, e0 + L) (keys and payload) into staging buffer b of the
+// calling warp; called by lane 0, completion counted on `bar`.
+template <class K, bool kVals>
+__device__ __forceinline__ void rss_issue(unsigned char* wbase, int b, uint64_t* bar, const K* keys,
+                                          const uint32_t* vals, uint32_t e0, uint32_t L) {
+  using WL = RssWarpLayout<K, kVals>;
+  const uintptr_t kb = reinterpret_cast<uintptr_t>(keys);
+  const uintptr_t ka = (kb + sizeof(K) * e0) & ~uintptr_t(15);
+  const uintptr_t kz = (kb + sizeof(K) * (e0 + L) + 15) & ~uintptr_t(15);
+  uint32_t bytes = static_cast<uint32_t>(kz - ka);
+  uintptr_t va = 0, vz = 0;
+  if constexpr (kVals) {
+    const uintptr_t vb = reinterpret_cast<uintptr_t>(vals);
+    va = (vb + 4ull * e0) & ~uintptr_t(15);
+    vz = (vb + 4ull * (e0 + L) + 15) & ~uintptr_t(15);
+    bytes += static_cast<uint32_t>(vz - va);
+  }
+  mbar_arrive_expect_tx(bar, bytes);
+  bulk_g2s(wbase + WL::kKeys + b * WL::kKeyCap, reinterpret_cast<const void*>(ka), static_cast<uint32_t>(kz - ka),
+           bar);
+  if constexpr (kVals)
+    bulk_g2s(wbase + WL::kVals_ + b * WL::kValCap, reinterpret_cast<const void*>(va),
+             static_cast<uint32_t>(vz - va), bar);
+}
+
+template <class K, bool kVals>
+__global__ void __launch_bounds__(kRssThreads, 2)
+    seg_rss_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
+                   const Plan* plan, const uint32_t* __restrict__ tile_first, const uint16_t* __restrict__ counts,
+                   const uint16_t* __restrict__ order, unsigned* status) {
+  using WL = RssWarpLayout<K, kVals>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  unsigned char* wbase = smem + warp * WL::kBytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + WL::kBar);
+  const RssMem<K> rm(wbase + WL::kScratch);
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  const uint32_t ntiles = plan->bad ? 0u : plan->ntiles;
+  const uint32_t gw = blockIdx.x * kRssWarps + warp;
+  const uint32_t W = gridDim.x * kRssWarps;
+
+  // Segment number d of this warp lives in staging buffer d & 1; its mbarrier
+  // phase is (d >> 1) & 1.  A segment is staged one step before it is sorted.
+  uint32_t issued = 0;
+  bool failed = false;
+  uint32_t pe0 = 0, pL = 0;  // the staged, not yet sorted segment (issued - 1)
+
+  auto sort_staged = [&](uint32_t d) {  // sort segment number d of this warp
+    const int b = d & 1;
+    if (!mbar_wait(&bar[b], (d >> 1) & 1u)) {
+      if (lane == 0) atomicOr(status, kStatusTimeout);
+      failed = true;
+      return;
+    }
+    K* kbuf = reinterpret_cast<K*>(wbase + WL::kKeys + b * WL::kKeyCap);
+    uint32_t* vbuf = reinterpret_cast<uint32_t*>(wbase + WL::kVals_ + b * WL::kValCap);
+    const uint32_t ks = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(keys + pe0) & 15) / sizeof(K));
+    const uint32_t vs = kVals ? static_cast<uint32_t>((reinterpret_cast<uintptr_t>(vals + pe0) & 15) / 4) : 0u;
+    rss_segment<K, kVals>(kbuf, vbuf, static_cast<int>(ks), static_cast<int>(vs), static_cast<int>(pL), rm, lane);
+    fence_proxy_async_smem();
+    __syncwarp();
+    store_range<K>(keys, kbuf, ks, pe0, pL, lane);
+    if constexpr (kVals) store_range<uint32_t>(vals, vbuf, vs, pe0, pL, lane);
+    if (lane == 0) {
+      bulk_commit();
+      bulk_wait_read<0>();  // the buffer is staged again two segments later
+    }
+    __syncwarp();
+  };
+
+  for (uint32_t chunk = gw; chunk < ntiles && !failed; chunk += 32u * W) {
+    const uint32_t t = chunk + lane * W;
+    uint32_t rc = 0, s0 = 0, base = 0;
+    if (t < ntiles) {
+      const uint4 c = *reinterpret_cast<const uint4*>(counts + 8ull * t);
+      rc = c.w & 0xFFFFu;  // counts[8t + 6]
+      if (rc) {
+        base = (c.x & 0xFFFFu) + (c.x >> 16) + (c.y & 0xFFFFu) + (c.y >> 16) + (c.z & 0xFFFFu) + (c.z >> 16);
+        s0 = tile_first[t];
+      }
+    }
+    unsigned mask = __ballot_sync(kFull, rc != 0);
+    while (mask && !failed) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const uint32_t rcj = __shfl_sync(kFull, rc, j), s0j = __shfl_sync(kFull, s0, j),
+                     basej = __shfl_sync(kFull, base, j);
+      for (uint32_t q0 = 0; q0 < rcj && !failed; q0 += 32) {
+        uint32_t e0q = 0, Lq = 0;
+        if (q0 + lane < rcj) {
+          const uint32_t local = order[s0j + basej + q0 + lane];
+          e0q = offsets[s0j + local];
+          Lq = offsets[s0j + local + 1] - e0q;
+        }
+        const uint32_t n = min(32u, rcj - q0);
+        for (uint32_t r = 0; r < n && !failed; ++r) {
+          const uint32_t ne0 = __shfl_sync(kFull, e0q, r), nL = __shfl_sync(kFull, Lq, r);
+          // stage segment number `issued`, then sort the previous one while it loads
+          if (lane == 0) rss_issue<K, kVals>(wbase, issued & 1, &bar[issued & 1], keys, vals, ne0, nL);
+          ++issued;
+          if (issued >= 2) sort_staged(issued - 2);
+          pe0 = ne0;
+          pL = nL;
+        }
+      }
+    }
+  }
+  if (issued >= 1 && !failed) sort_staged(issued - 1);
+  if (lane == 0) bulk_wait_all<0>();
 }
 
 // ------------------------------------------------------------ host side ----
 
-inline uint64_t tile_capacity(uint64_t nseg, uint32_t E) {
-  // tiles for valid offsets: u_{nseg-1} <= 257 (nseg - 1); one extra entry
-  return (257ull * (nseg - 1)) / E + 2;
-}
-
-template <class K, bool kVals, bool kRssOnly>
-cudaError_t launch_sort(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, void* scratch,
-                        const SegTuning& tun, cudaStream_t stream, const DeviceInfo& d) {
+template <class K, bool kVals>
+cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, bool rss_only,
+                       void* scratch, const SegTuning& tun, cudaStream_t stream, const DeviceInfo& d) {
   const uint32_t E = static_cast<uint32_t>(tun.tile_units);
-  Plan* plan = reinterpret_cast<Plan*>(scratch);
-  uint32_t* tile_first = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(scratch) + 256);
-  const uint64_t cap = tile_capacity(nseg, E);
+  const ScratchLayout sl(nseg, E);
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  Plan* plan = reinterpret_cast<Plan*>(base + sl.plan_at);
+  uint32_t* tile_first = reinterpret_cast<uint32_t*>(base + sl.tile_first_at);
+  uint16_t* counts = reinterpret_cast<uint16_t*>(base + sl.counts_at);
+  uint16_t* order = reinterpret_cast<uint16_t*>(base + sl.order_at);
 
   cudaError_t e = cudaMemsetAsync(plan, 0, sizeof(Plan), stream);
   if (e != cudaSuccess) return e;
   const uint64_t want = (nseg + 255) / 256;
   const unsigned g1 = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(want, 16ull * d.sm_count)));
-  seg_plan_kernel<<<g1, 256, 0, stream>>>(offsets, nseg, E, plan, tile_first, cap, d.status);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  seg_plan_kernel<<<g1, 256, 0, stream>>>(offsets, nseg, E, plan, tile_first, sl.cap, d.status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const unsigned g2 = static_cast<unsigned>(std::max<uint64_t>(
+      1, std::min<uint64_t>(sl.cap - 1, 8ull * d.sm_count)));
+  seg_bin_kernel<<<g2, 256, 0, stream>>>(offsets, plan, tile_first, counts, order, rss_only);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-  const Layout<K, kVals> lay(E);
-  const int smem_bytes = static_cast<int>(lay.total);
-  auto kern = seg_sort_kernel<K, kVals, kRssOnly>;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem_bytes);
-  if (e != cudaSuccess) return e;
-  per_sm = std::max(per_sm, 1);
-  const uint64_t max_tiles = cap - 1;
-  const unsigned g2 = static_cast<unsigned>(
-      std::max<uint64_t>(1, std::min<uint64_t>(max_tiles, static_cast<uint64_t>(d.sm_count) * per_sm)));
-  kern<<<g2, kThreads, smem_bytes, stream>>>(keys, vals, offsets, plan, plan, tile_first, E, d.status);
-  return cudaGetLastError();
+  {
+    const TileLayout<K, kVals> lay(E);
+    const int smem_bytes = static_cast<int>(lay.total);
+    auto kern = seg_tile_kernel<K, kVals>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes)) != cudaSuccess)
+      return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem_bytes)) !=
+        cudaSuccess)
+      return e;
+    per_sm = std::max(per_sm, 1);
+    const unsigned g3 = static_cast<unsigned>(
+        std::max<uint64_t>(1, std::min<uint64_t>(sl.cap - 1, static_cast<uint64_t>(d.sm_count) * per_sm)));
+    kern<<<g3, kTileThreads, smem_bytes, stream>>>(keys, vals, offsets, plan, tile_first, counts, order, E,
+                                                   d.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    using WL = RssWarpLayout<K, kVals>;
+    const int smem_bytes = static_cast<int>(kRssWarps * WL::kBytes);
+    auto kern = seg_rss_kernel<K, kVals>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes)) != cudaSuccess)
+      return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRssThreads, smem_bytes)) !=
+        cudaSuccess)
+      return e;
+    per_sm = std::max(per_sm, 1);
+    const uint64_t tiles_cap = sl.cap - 1;
+    const unsigned g4 = static_cast<unsigned>(std::max<uint64_t>(
+        1, std::min<uint64_t>((tiles_cap + kRssWarps - 1) / kRssWarps, static_cast<uint64_t>(d.sm_count) * per_sm)));
+    kern<<<g4, kRssThreads, smem_bytes, stream>>>(keys, vals, offsets, plan, tile_first, counts, order, d.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <class K>
 cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,
                             void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
                             const DeviceInfo& d) {
-  if (scratch_bytes < segments_scratch_bytes(nseg, t)) return cudaErrorInvalidValue;
   if (t.tile_units < 512 || t.tile_units > 8192) return cudaErrorInvalidValue;
+  if (scratch_bytes < ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total) return cudaErrorInvalidValue;
   const bool rss = mode == SegMode::kRssOnly;
-  if (vals) {
-    return rss ? launch_sort<K, true, true>(keys, vals, offsets, nseg, scratch, t, s, d)
-               : launch_sort<K, true, false>(keys, vals, offsets, nseg, scratch, t, s, d);
-  }
-  return rss ? launch_sort<K, false, true>(keys, vals, offsets, nseg, scratch, t, s, d)
-             : launch_sort<K, false, false>(keys, vals, offsets, nseg, scratch, t, s, d);
+  return vals ? launch_all<K, true>(keys, vals, offsets, nseg, rss, scratch, t, s, d)
+              : launch_all<K, false>(keys, vals, offsets, nseg, rss, scratch, t, s, d);
 }
 
 }  // namespace

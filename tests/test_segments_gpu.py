@@ -55,6 +55,17 @@ def test_segments_parity(mode, dtype, with_vals, lengths, lo, hi):
 
 
 @pytest.mark.parametrize("mode", ["sn", "rss"])
+@pytest.mark.parametrize("lengths,lo,hi", [("uniform", 1, 16), ("geometric", 1, 256), ("uniform", 1, 256)])
+def test_segments_many_tiles(mode, lengths, lo, hi):
+    # enough segments that every persistent CTA reuses its staging buffers
+    # many times (the full-size workloads' steady state), compared in full
+    k, v, off = wl.segment_batch(1 << 18, lengths, "uniform", np.uint64, True, seed=21, lo=lo, hi=hi)
+    assert_parity(mode, k, v, off)
+    k32 = (k >> np.uint64(40)).astype(np.uint32)
+    assert_parity(mode, k32, None, off)
+
+
+@pytest.mark.parametrize("mode", ["sn", "rss"])
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
 def test_segments_every_length(mode, dtype):
     # every length 0..256, several of each, shuffled
