@@ -99,6 +99,33 @@ int rss_sort_segments_u64(uint64_t *keys, uint32_t *vals, const uint32_t *offset
                           uint64_t nseg, sn_stream_t stream);
 
 /*
+ * sn_sort_segments_u64 without any allocation.  (Library addition: the paper
+ * has no counterpart.)  For callers that cannot allocate device memory at the
+ * time they sort -- a process that reserved its whole device budget up front,
+ * a thread that must not enter the allocator (a real-time loop, a callback
+ * running under the allocator's lock), a framework that only hands out buffers
+ * it manages.  Same contract and results as sn_sort_segments_u64, with these
+ * differences:
+ *   - scratch is a fixed device array inside the library (about 1.2 MB per GPU
+ *     that loads the library, kept until the process exits); no cudaMalloc,
+ *     cudaFree or pool allocation happens in the call;
+ *   - nseg must be at most SN_NOALLOC_MAX_SEGMENTS, else SN_ERANGE (nothing
+ *     is launched);
+ *   - the first call on each device does a one-time set-up on the calling
+ *     thread (it looks up the device addresses of that array and of the status
+ *     word, which may load the library's device code); make that first call
+ *     before any stream capture on the device;
+ *   - every call on a device uses the same array, and the last call's plan
+ *     stays in it; calls whose work overlaps on the GPU (different streams
+ *     without ordering between them) race on it and give wrong results --
+ *     order such calls on one stream or with events.
+ * Device-detected errors land in the status word that sn_check() reports.
+ */
+#define SN_NOALLOC_MAX_SEGMENTS 262144
+int sn_sort_segments_u64_noalloc(uint64_t *keys, uint32_t *vals, const uint32_t *offsets,
+                                 uint64_t nseg, sn_stream_t stream);
+
+/*
  * Synchronises `stream`, then returns and clears the device status word of the
  * current device: SN_ERANGE if a segmented call met bad offsets, SN_ETIMEOUT
  * if a bounded device wait ran out, SN_ECUDA if the stream reported a CUDA

@@ -199,3 +199,89 @@ const char* sn_status_string(int status) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Segmented sort without any allocation (sn_sort_segments_u64_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they sort: code
+// running on a fixed device-memory budget that was reserved up front, hosts
+// whose allocator must not be entered from the sorting thread (a real-time
+// loop, a callback that holds the allocator's lock), or frameworks that only
+// hand out the buffers they manage.  This entry point serves them: its
+// scratch is the file-scope array below, which every GPU that loads the
+// library keeps until the process exits, so the call itself allocates
+// nothing.  The kernels are the ones sn_sort_segments_u64 runs.
+// ---------------------------------------------------------------------------
+
+#include "sn_segments.cuh"
+
+namespace sn {
+namespace {
+
+constexpr uint64_t kNoAllocMaxSegments = SN_NOALLOC_MAX_SEGMENTS;
+constexpr uint32_t kNoAllocTileUnits = 2048;
+constexpr size_t kNoAllocScratchBytes = seg::ScratchLayout(kNoAllocMaxSegments, kNoAllocTileUnits).total;
+
+// Shared by every call on a device; holds the last call's plan and bins.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+  DeviceInfo info;
+  void* scratch = nullptr;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc[kMaxDevices];
+std::atomic<bool> g_noalloc_ready[kMaxDevices];
+
+// Once per device, with that device current: device facts and the device
+// addresses of the scratch array and the status word (host code cannot use
+// the arrays' names as device addresses).
+int noalloc_setup(int dev, NoAllocDevice* out) {
+  NoAllocDevice nd;
+  nd.info.device = dev;
+  if (cudaDeviceGetAttribute(&nd.info.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SN_ECUDA;
+  if (cudaDeviceGetAttribute(&nd.info.cc_major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess)
+    return SN_ECUDA;
+  if (cudaDeviceGetAttribute(&nd.info.cc_minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+    return SN_ECUDA;
+  if (nd.info.cc_major != 10 || nd.info.cc_minor != 3) return SN_EUNSUPPORTED;
+  void* status = nullptr;
+  if (cudaGetSymbolAddress(&status, g_status) != cudaSuccess) return SN_EUNSUPPORTED;
+  nd.info.status = static_cast<unsigned*>(status);
+  void* scratch = nullptr;
+  if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess) return SN_EUNSUPPORTED;
+  nd.scratch = scratch;
+  *out = nd;
+  return SN_OK;
+}
+
+}  // namespace
+}  // namespace sn
+
+extern "C" int sn_sort_segments_u64_noalloc(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
+                                            sn_stream_t stream) {
+  if (nseg == 0) return SN_OK;
+  if (keys == nullptr || offsets == nullptr) return SN_EINVAL;
+  if (nseg > sn::kNoAllocMaxSegments) return SN_ERANGE;
+  if (reinterpret_cast<uintptr_t>(keys) % 8 != 0 || reinterpret_cast<uintptr_t>(offsets) % 4 != 0 ||
+      reinterpret_cast<uintptr_t>(vals) % 4 != 0)
+    return SN_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SN_ECUDA;
+  if (dev < 0 || dev >= sn::kMaxDevices) return SN_EUNSUPPORTED;
+  if (!sn::g_noalloc_ready[dev].load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lock(sn::g_noalloc_mu);
+    if (!sn::g_noalloc_ready[dev].load(std::memory_order_relaxed)) {
+      const int rc = sn::noalloc_setup(dev, &sn::g_noalloc[dev]);
+      if (rc != SN_OK) return rc;
+      sn::g_noalloc_ready[dev].store(true, std::memory_order_release);
+    }
+  }
+  const sn::NoAllocDevice& nd = sn::g_noalloc[dev];
+  sn::SegTuning tun;
+  tun.tile_units = static_cast<int>(sn::kNoAllocTileUnits);
+  const cudaError_t e = sn::seg::launch_segments<uint64_t>(keys, vals, offsets, nseg, sn::SegMode::kNetworkWarpRss,
+                                                           nd.scratch, sn::kNoAllocScratchBytes, tun,
+                                                           reinterpret_cast<cudaStream_t>(stream), nd.info);
+  return e == cudaSuccess ? SN_OK : SN_ECUDA;
+}

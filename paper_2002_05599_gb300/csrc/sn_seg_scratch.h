@@ -20,19 +20,18 @@ struct ScratchLayout {
   uint64_t cap;  // entries of the tile tables (an upper bound on tiles + 1)
   size_t plan_at, tile_first_at, counts_at, order_at, total;
 
-  static size_t up256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+  static constexpr size_t up256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
   // nseg segments, tiles of E units (segments + items).  For valid offsets
   // segment s starts at unit u_s <= 257 s, so at most 257 (nseg - 1) / E + 1
   // tiles exist.
-  ScratchLayout(uint64_t nseg, uint32_t E) {
-    cap = nseg ? (257ull * (nseg - 1)) / E + 2 : 2;
-    plan_at = 0;
-    tile_first_at = up256(sizeof(Plan));
-    counts_at = up256(tile_first_at + cap * 4);
-    order_at = up256(counts_at + cap * 16);
-    total = up256(order_at + (nseg + 8) * 2);
-  }
+  constexpr ScratchLayout(uint64_t nseg, uint32_t E)
+      : cap(nseg ? (257ull * (nseg - 1)) / E + 2 : 2),
+        plan_at(0),
+        tile_first_at(up256(sizeof(Plan))),
+        counts_at(up256(tile_first_at + cap * 4)),
+        order_at(up256(counts_at + cap * 16)),
+        total(up256(order_at + (nseg + 8) * 2)) {}
 };
 
 }  // namespace seg
