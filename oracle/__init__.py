@@ -138,8 +138,8 @@ def network_depth(n: int, pairs) -> int:
     return int(_load().oracle_network_depth(n, _ptr(lo), _ptr(hi), len(lo)))
 
 
-# Permutation check constants: p is a large prime (Sec. 4.1 asks for "a
-# (preferably large) prime"); z is arbitrary and is bumped until v != 0.
+# Permutation check constants: p is a large prime (Sec. 4.1 leaves the prime
+# open); z is arbitrary and is increased until v != 0.
 PERM_P = (1 << 61) - 1
 PERM_Z = 0x2545F4914F6CDD1D % PERM_P
 

@@ -23,7 +23,7 @@ from __future__ import annotations
 
 
 def sample_positions(length: int, count: int) -> list[int]:
-    """Equidistant sample positions (this library's reading of 'a sample subset')."""
+    """Equidistant sample positions (this library's reading; the paper leaves the choice open)."""
     return [((2 * i + 1) * length) // (2 * count) for i in range(count)]
 
 

@@ -435,7 +435,7 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
   const int logB = __ffs(B) - 1;
   const int S = 2 * B;
 
-  // 1. equidistant sample (this library's reading of "a sample subset"),
+  // 1. equidistant sample (this library's reading; the paper leaves the choice open),
   //    sorted by a bitonic network; kept in slots 0..S-1
   for (int q = lane; q < S; q += 32) {
     const int pos = ((2 * q + 1) * L) / (2 * S);
