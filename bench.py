@@ -145,42 +145,58 @@ class ClockSampler:
 
 # --------------------------------------------------------------- our arm ----
 
-def make_inputs(sizes, device, rank):
+def make_inputs(sizes, device, rank, parts=("sweep", "uneven", "rss")):
     import torch
     from paper_2002_05599_gb300 import workloads as wl
     seed = 1 + rank
     inp = {}
-    for n in SWEEP_NS:
-        inp[f"sweep{n}"] = wl.uniform_keys_torch(sizes["sweep_count"] * n, np.uint32, seed=seed * 1000 + n,
-                                                 device=device)
-    lens = wl.segment_lengths(sizes["uneven_nseg"], "geometric", seed=seed, p=0.15, cap=256)
-    off = wl.offsets_from_lengths(lens)
-    total = int(off[-1])
-    inp["uneven_off"] = torch.from_numpy(off.view(np.int32)).to(device)
-    inp["uneven_keys"] = wl.uniform_keys_torch(total, np.uint64, seed=seed, device=device)
-    inp["uneven_vals"] = torch.arange(total, dtype=torch.int32, device=device)
-    lens = wl.segment_lengths(sizes["rss_nseg"], "uniform", seed=seed + 100, lo=17, hi=256)
-    off = wl.offsets_from_lengths(lens)
-    inp["rss_off"] = torch.from_numpy(off.view(np.int32)).to(device)
-    inp["rss_keys"] = wl.uniform_keys_torch(int(off[-1]), np.uint32, seed=seed + 100, device=device)
+    if "sweep" in parts:
+        for n in SWEEP_NS:
+            inp[f"sweep{n}"] = wl.uniform_keys_torch(sizes["sweep_count"] * n, np.uint32, seed=seed * 1000 + n,
+                                                     device=device)
+    if "uneven" in parts:
+        lens = wl.segment_lengths(sizes["uneven_nseg"], "geometric", seed=seed, p=0.15, cap=256)
+        off = wl.offsets_from_lengths(lens)
+        total = int(off[-1])
+        inp["uneven_off"] = torch.from_numpy(off.view(np.int32)).to(device)
+        inp["uneven_keys"] = wl.uniform_keys_torch(total, np.uint64, seed=seed, device=device)
+        inp["uneven_vals"] = torch.arange(total, dtype=torch.int32, device=device)
+    if "rss" in parts:
+        lens = wl.segment_lengths(sizes["rss_nseg"], "uniform", seed=seed + 100, lo=17, hi=256)
+        off = wl.offsets_from_lengths(lens)
+        inp["rss_off"] = torch.from_numpy(off.view(np.int32)).to(device)
+        inp["rss_keys"] = wl.uniform_keys_torch(int(off[-1]), np.uint32, seed=seed + 100, device=device)
     return inp
 
 
 def part_keys(inp):
-    sweep = sum(inp[f"sweep{n}"].numel() for n in SWEEP_NS)
-    return {"sweep": sweep, "uneven": inp["uneven_keys"].numel(), "rss": inp["rss_keys"].numel()}
+    out = {}
+    if "sweep2" in inp:
+        out["sweep"] = sum(inp[f"sweep{n}"].numel() for n in SWEEP_NS)
+    if "uneven_keys" in inp:
+        out["uneven"] = inp["uneven_keys"].numel()
+    if "rss_keys" in inp:
+        out["rss"] = inp["rss_keys"].numel()
+    return out
 
 
 def part_bytes(inp):
     """Algorithmic bytes per step: every key / payload read and written once,
     offsets read once."""
-    sweep = 8 * sum(inp[f"sweep{n}"].numel() for n in SWEEP_NS)
-    uneven = 2 * (8 + 4) * inp["uneven_keys"].numel() + 4 * inp["uneven_off"].numel()
-    rss = 2 * 4 * inp["rss_keys"].numel() + 4 * inp["rss_off"].numel()
-    return {"sweep": sweep, "uneven": uneven, "rss": rss}
+    out = {}
+    if "sweep2" in inp:
+        out["sweep"] = 8 * sum(inp[f"sweep{n}"].numel() for n in SWEEP_NS)
+    if "uneven_keys" in inp:
+        out["uneven"] = 2 * (8 + 4) * inp["uneven_keys"].numel() + 4 * inp["uneven_off"].numel()
+    if "rss_keys" in inp:
+        out["rss"] = 2 * 4 * inp["rss_keys"].numel() + 4 * inp["rss_off"].numel()
+    return out
 
 
-LAUNCHES_PER_STEP = len(SWEEP_NS) + 4 + 4  # fixed-n launches + (plan, bin, tile, rss) x 2
+def launches_per_step(parts=("sweep", "uneven", "rss")):
+    """Kernels of this library launched per step: one per fixed n, and plan,
+    bin, tile and RSS kernels per segmented call."""
+    return (len(SWEEP_NS) if "sweep" in parts else 0) + 4 * sum(p in parts for p in ("uneven", "rss"))
 
 
 PARTS = ("sweep", "uneven", "rss")
@@ -212,17 +228,18 @@ def bench_ours(args, rank, world, local_rank, dist):
     device = torch.device("cuda", local_rank)
     torch.cuda.set_device(device)
     sizes = workload_sizes(args.scale)
-    pristine = make_inputs(sizes, device, rank)
+    parts = tuple(p for p in args.parts.split(",") if p)
+    pristine = make_inputs(sizes, device, rank, parts)
     work = {k: v.clone() for k, v in pristine.items()}
     keys = part_keys(pristine)
     bytes_ = part_bytes(pristine)
     total_keys = sum(keys.values())
 
     def restore():
-        for k in ("uneven_keys", "uneven_vals", "rss_keys", *[f"sweep{n}" for n in SWEEP_NS]):
-            work[k].copy_(pristine[k])
+        for k, v in work.items():
+            if not k.endswith("_off"):
+                v.copy_(pristine[k])
 
-    parts = tuple(p for p in args.parts.split(",") if p)
     for _ in range(args.warmup):
         restore()
         run_parts(sn, work, parts=parts)
@@ -264,7 +281,7 @@ def bench_ours(args, rank, world, local_rank, dist):
         ms = dict(zip(["step", "sweep", "uneven", "rss"], t.tolist()))
 
     hbm, hbm_src = peaks()
-    sweep_gbs = bytes_["sweep"] / (ms["sweep"] * 1e-3) / 1e9
+    sweep_gbs = bytes_["sweep"] / (ms["sweep"] * 1e-3) / 1e9 if "sweep" in parts else 0.0
     parts_out = {}
     for p in parts:
         gbs = bytes_[p] / (ms[p] * 1e-3) / 1e9
@@ -290,20 +307,20 @@ def bench_ours(args, rank, world, local_rank, dist):
         "roofline": {"bound": "hbm", "kernel": "fixed_tma_kernel (n=2..16, sweep)",
                      "achieved": round(sweep_gbs, 1), "peak": hbm, "peak_source": hbm_src,
                      "unit": "GB/s", "frac": round(sweep_gbs / hbm, 4), "traffic": None},
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": launches_per_step(parts) * args.steps,
         "clocks": clocks,
         "wall_s_timed_loop": round(wall, 3),
     }
 
     if not args.no_e2e:
-        result["e2e"] = bench_e2e(args, sn, pristine, world, dist, device)
+        result["e2e"] = bench_e2e(args, sn, pristine, world, dist, device, parts)
     del work
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(sizes, budget_s=12.0)
     return result
 
 
-def bench_e2e(args, sn, pristine, world, dist, device):
+def bench_e2e(args, sn, pristine, world, dist, device, parts=PARTS):
     """The same step through the C ABI with host buffers (pinned)."""
     import torch
     host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in pristine.items()}
@@ -318,7 +335,7 @@ def bench_e2e(args, sn, pristine, world, dist, device):
     def step():
         for k, v in host.items():
             dev[k].copy_(v, non_blocking=True)
-        run_parts(sn, dev)
+        run_parts(sn, dev, parts=parts)
         for k, v in out.items():
             v.copy_(dev[k], non_blocking=True)
 
