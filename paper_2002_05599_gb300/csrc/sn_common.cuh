@@ -137,6 +137,12 @@ __device__ __forceinline__ Item64 shfl_xor(const Item64& v, int m) {
   return Item64{__shfl_xor_sync(0xFFFFFFFFu, v.key, m), __shfl_xor_sync(0xFFFFFFFFu, v.idx, m)};
 }
 
+__device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int src) { return __shfl_sync(0xFFFFFFFFu, v, src); }
+__device__ __forceinline__ uint64_t shfl_idx(uint64_t v, int src) { return __shfl_sync(0xFFFFFFFFu, v, src); }
+__device__ __forceinline__ Item64 shfl_idx(const Item64& v, int src) {
+  return Item64{__shfl_sync(0xFFFFFFFFu, v.key, src), __shfl_sync(0xFFFFFFFFu, v.idx, src)};
+}
+
 // 32-lane warp network (generated schedule): lane l meets lane l ^ M at every
 // step; the lower lane keeps the smaller item.
 template <class T>

@@ -26,7 +26,9 @@ cudaError_t launch_fixed_u64(uint64_t* keys, int n, uint64_t count, cudaStream_t
 enum class SegMode : int { kNetworkWarpRss = 0, kRssOnly = 1 };
 
 struct SegTuning {
-  int tile_units = 2048;  // segments + elements per tile (512..8192)
+  int tile_units = 2048;       // segments + elements per tile (512..8192)
+  uint32_t net_classes = 0xF;  // padded network classes in use: bit q = 2, 4, 8, 12 channels (16 always)
+  int rss_two_min = 160;       // RSS segments longer than this take a 64-item sample, else 32 (16..256)
 };
 
 // Device scratch needed for a segmented call with nseg segments.

@@ -40,6 +40,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 
 #include "sn_common.cuh"
 #include "sn_internal.h"
@@ -57,7 +58,7 @@ constexpr int kRssWarps = 8;
 constexpr int kRssThreads = kRssWarps * 32;
 constexpr int kMaxSeg = 256;
 constexpr uint32_t kDone = 0xFFFFFFFFu;
-constexpr int kRssMaxBuckets = 64;
+constexpr int kRssMaxBuckets = 32;  // one bucket per lane
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Classes handled by the tile kernel, in list and hand-out order.
@@ -65,12 +66,15 @@ enum TileCls : int { kPair = 0, kNet16, kNet12, kNet8, kNet4, kNet2, kNumTileCls
 constexpr int kRssCls = kNumTileCls;
 constexpr int kSkipCls = kNumTileCls + 1;
 
-__device__ __forceinline__ int seg_class(uint32_t len, bool rss_only) {
+// Bit q of `net_mask` enables the padded network class 2, 4, 8, 12 (q = 0..3);
+// a segment of 2..16 items takes the smallest enabled class that holds it,
+// 16 channels if none does.
+__device__ __forceinline__ int seg_class(uint32_t len, bool rss_only, uint32_t net_mask) {
   if (len <= 1) return kSkipCls;
-  if (len == 2) return kNet2;
-  if (len <= 4) return kNet4;
-  if (len <= 8) return kNet8;
-  if (len <= 12) return kNet12;
+  if (len == 2 && (net_mask & 1u)) return kNet2;
+  if (len <= 4 && (net_mask & 2u)) return kNet4;
+  if (len <= 8 && (net_mask & 4u)) return kNet8;
+  if (len <= 12 && (net_mask & 8u)) return kNet12;
   if (len <= 16) return kNet16;
   if (len <= 32 && !rss_only) return kPair;
   return kRssCls;
@@ -190,7 +194,8 @@ __global__ void __launch_bounds__(256)
 // in registers (warp-uniform); positions come from ballots.
 __global__ void __launch_bounds__(256)
     seg_bin_kernel(const uint32_t* __restrict__ offsets, const Plan* plan, const uint32_t* __restrict__ tile_first,
-                   uint16_t* __restrict__ counts, uint16_t* __restrict__ order, bool rss_only) {
+                   uint16_t* __restrict__ counts, uint16_t* __restrict__ order, bool rss_only,
+                   uint32_t net_mask) {
   constexpr int kCls = kNumTileCls + 1;  // tile classes + RSS
   const int lane = threadIdx.x & 31;
   const unsigned ntiles = plan->bad ? 0u : plan->ntiles;
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(256)
     for (int q = 0; q < kCls; ++q) cnt[q] = 0;
     for (uint32_t i0 = 0; i0 < ns; i0 += 32) {
       const uint32_t i = i0 + lane;
-      const int c = i < ns ? seg_class(offsets[s0 + i + 1] - offsets[s0 + i], rss_only) : kSkipCls;
+      const int c = i < ns ? seg_class(offsets[s0 + i + 1] - offsets[s0 + i], rss_only, net_mask) : kSkipCls;
 #pragma unroll
       for (int q = 0; q < kCls; ++q) cnt[q] += __popc(__ballot_sync(kFull, c == q));
     }
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(256)
     if (lane == 7) counts[8ull * t + 7] = 0;
     for (uint32_t i0 = 0; i0 < ns; i0 += 32) {
       const uint32_t i = i0 + lane;
-      const int c = i < ns ? seg_class(offsets[s0 + i + 1] - offsets[s0 + i], rss_only) : kSkipCls;
+      const int c = i < ns ? seg_class(offsets[s0 + i + 1] - offsets[s0 + i], rss_only, net_mask) : kSkipCls;
 #pragma unroll
       for (int q = 0; q < kCls; ++q) {
         const unsigned m = __ballot_sync(kFull, c == q);
@@ -423,127 +428,147 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K>& rm, int st, i
   }
 }
 
+// Register Sample Sort of one segment of L (17..256) items by one warp
+// (Sec. 3).  Items are (key, position-in-segment) pairs, all distinct.
+//
+//  1. sample: a*32 items at equidistant positions (a = 1, or 2 above
+//     `two_min` items), sorted in registers by the 32-lane warp network
+//     (two halves merged for a = 2);
+//  2. splitters s_j = S_{j*a}, j = 1..31, as a heap-ordered tree held one node
+//     per lane (lane t holds node t) and broadcast by __shfl;
+//  3. classify: every item descends j <- 2j + [t_j < e] five times, so bucket
+//     b = j - 32 holds s_b < e <= s_{b+1}; its rank inside the bucket comes
+//     from a shared-memory counter (any order will do: each bucket is sorted
+//     afterwards);
+//  4. bucket starts by a warp scan (lane b owns bucket b);
+//  5. scatter the items into the shared item buffer;
+//  6. lane b sorts bucket b with a network padded to the warp's largest bucket
+//     of at most 16 items (4, 8, 12 or 16 channels); buckets above 16 items
+//     (rare) are sorted by the whole warp (32-lane network, or a bitonic pass
+//     in shared memory above 32);
+//  7. write back (payload gathered by original position).
 template <class K, bool kVals>
 __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, const RssMem<K>& rm,
-                                            int lane) {
+                                            int lane, int two_min) {
   using IO = ItemOf<K>;
   using It = typename IO::T;
 
-  // k buckets with at most L/4 expected items each (k in 8..64), sample of 2k
-  int B = 8;
-  while (B * 4 < L) B <<= 1;
-  const int logB = __ffs(B) - 1;
-  const int S = 2 * B;
-
-  // 1. equidistant sample (this library's reading; the paper leaves the choice open),
-  //    sorted by a bitonic network; kept in slots 0..S-1
-  for (int q = lane; q < S; q += 32) {
-    const int pos = ((2 * q + 1) * L) / (2 * S);
-    rm.set(q, IO::make(kbuf[p + pos], pos));
-  }
-  __syncwarp();
-  warp_bitonic_smem<K, false>(rm, 0, S, lane);
-
-  // 2. splitters s_j = S_{2j} (1-based), heap-ordered tree in slots S+1..S+k-1
-  for (int node = lane; node < B; node += 32) {
-    if (node >= 1) {
-      const int d = 31 - __clz(node);
-      const int pos = node - (1 << d);
-      const int rank = (2 * pos + 1) * (B >> (d + 1));
-      rm.set(S + node, rm.get(2 * rank - 1));
+  // 1. sorted sample: slot q < 32 in s0 of lane q, slot 32 + q in s1 of lane q
+  const bool two = L > two_min;
+  const int S = two ? 64 : 32;
+  It s0, s1;
+  {
+    const int q0 = ((2 * lane + 1) * L) / (2 * S);
+    s0 = IO::make(kbuf[p + q0], q0);
+    warp_network32(s0, lane);
+    if (two) {
+      const int q1 = ((2 * (32 + lane) + 1) * L) / (2 * S);
+      s1 = IO::make(kbuf[p + q1], q1);
+      warp_network32(s1, lane);
+      // merge two ascending halves: slot l meets slot 63 - l; the smaller
+      // items form a bitonic lower half, the larger a bitonic upper half
+      // (in reversed lane order, still bitonic), each sorted by the
+      // half-cleaners 16, 8, 4, 2, 1
+      const It y = shfl_idx(s1, 31 - lane);
+      It lo = pick(s0, y, true), hi = pick(s0, y, false);
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) {
+        const bool keep_min = lane < (lane ^ m);
+        lo = pick(lo, shfl_xor(lo, m), keep_min);
+        hi = pick(hi, shfl_xor(hi, m), keep_min);
+      }
+      s0 = lo;
+      s1 = hi;
     }
   }
-  for (int b = lane; b < B; b += 32) rm.cnt[b] = 0;
+
+  // 2. tree node t (depth d, position p_d) = splitter (2 p_d + 1) * 2^(4 - d)
+  //    = sample slot a * that - 1
+  It tree;
+  {
+    const int t = lane > 0 ? lane : 1;
+    const int d = 31 - __clz(t);
+    const int rank = (2 * (t - (1 << d)) + 1) << (4 - d);
+    const int slot = two ? 2 * rank - 1 : rank - 1;
+    const It from0 = shfl_idx(s0, slot & 31);
+    tree = from0;
+    if (two) {
+      const It from1 = shfl_idx(s1, slot & 31);
+      tree = slot >= 32 ? from1 : from0;
+    }
+  }
+  rm.cnt[lane] = 0;
   __syncwarp();
 
-  // 3. classify (j <- 2j + [t_j < e]) and rank items stably within buckets
+  // 3. classify the register-resident items (item e = 32 r + lane)
   const int rounds = (L + 31) >> 5;
-  uint32_t packed[8];
+  It x[8];
+  int j[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    packed[r] = 0;
-    if (r < rounds) {
-      const int e = (r << 5) + lane;
-      const bool valid = e < L;
-      const It x = valid ? IO::make(kbuf[p + e], e) : IO::sentinel(0);
-      int j = 1;
-      for (int lv = 0; lv < logB; ++lv) j = 2 * j + (item_less(rm.get(S + j), x) ? 1 : 0);
-      const int b = j - B;
-      unsigned peers = __ballot_sync(kFull, valid);
-      for (int bit = 0; bit < logB; ++bit) {
-        const unsigned m = __ballot_sync(kFull, (b >> bit) & 1);
-        peers &= ((b >> bit) & 1) ? m : ~m;
+    j[r] = 1;
+    const int e = (r << 5) + lane;
+    x[r] = (r < rounds && e < L) ? IO::make(kbuf[p + e], e) : IO::sentinel(0);
+  }
+#pragma unroll
+  for (int lv = 0; lv < 5; ++lv) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if (r < rounds) {
+        const It t = shfl_idx(tree, j[r]);
+        j[r] = 2 * j[r] + (item_less(t, x[r]) ? 1 : 0);
       }
-      const unsigned before = valid ? rm.cnt[b] : 0;
-      __syncwarp();
-      const unsigned below = __popc(peers & ((1u << lane) - 1u));
-      if (valid && below == 0) rm.cnt[b] = before + __popc(peers);
-      __syncwarp();
-      packed[r] = (static_cast<uint32_t>(b) << 16) | (before + below);
     }
   }
+  uint32_t rank_in[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    rank_in[r] = 0;
+    if (r < rounds && (r << 5) + lane < L) rank_in[r] = atomicAdd(&rm.cnt[j[r] - 32], 1u);
+  }
+  __syncwarp();
 
-  // 4. bucket starts: exclusive scan over the k counters, lane l owns buckets
-  //    l and l + 32
-  const uint32_t c0 = lane < B ? rm.cnt[lane] : 0;
-  const uint32_t c1 = lane + 32 < B ? rm.cnt[lane + 32] : 0;
-  uint32_t incl = c0;
+  // 4. bucket starts (lane b owns bucket b)
+  const uint32_t c = rm.cnt[lane];
+  uint32_t incl = c;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const uint32_t y = __shfl_up_sync(kFull, incl, d);
     if (lane >= d) incl += y;
   }
-  const uint32_t start0 = incl - c0;
-  const uint32_t total0 = __shfl_sync(kFull, incl, 31);
-  uint32_t incl1 = c1;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, incl1, d);
-    if (lane >= d) incl1 += y;
-  }
-  const uint32_t start1 = total0 + incl1 - c1;
-  __syncwarp();
+  const uint32_t start = incl - c;
 
-  // 5. stable scatter into the item buffer (overwrites sample and tree)
+  // 5. scatter into the item buffer
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     if (r < rounds) {
-      const int e = (r << 5) + lane;
-      const int b = static_cast<int>(packed[r] >> 16);
-      const uint32_t s_lo = __shfl_sync(kFull, start0, b & 31);
-      const uint32_t s_hi = __shfl_sync(kFull, start1, b & 31);
-      const uint32_t st = b < 32 ? s_lo : s_hi;
-      if (e < L) rm.set(static_cast<int>(st + (packed[r] & 0xFFFFu)), IO::make(kbuf[p + e], e));
+      const uint32_t st = __shfl_sync(kFull, start, (j[r] - 32) & 31);
+      if ((r << 5) + lane < L) rm.set(static_cast<int>(st + rank_in[r]), x[r]);
     }
   }
   __syncwarp();
 
-  // 6. finish every bucket with a network: every lane pads its buckets to the
-  //    warp's largest bucket (network of 4, 8, 12 or 16 channels); buckets
-  //    above 16 items (rare) are sorted afterwards by the whole warp
-  const uint32_t maxc = __reduce_max_sync(kFull, max(c0, c1));
-  const int m = static_cast<int>(maxc < 16 ? maxc : 16);
-  if (m >= 2) {
-    if (lane < B && c0 <= 16) bucket_network_class<K, kVals>(m, rm, static_cast<int>(start0), static_cast<int>(c0));
-    if (lane + 32 < B && c1 <= 16)
-      bucket_network_class<K, kVals>(m, rm, static_cast<int>(start1), static_cast<int>(c1));
-  }
+  // 6. one bucket per lane, network padded to the warp's largest bucket <= 16
+  const uint32_t m = __reduce_max_sync(kFull, c <= 16 ? c : 0u);
+  if (m >= 2 && c <= 16) bucket_network_class<K, kVals>(static_cast<int>(m), rm, static_cast<int>(start),
+                                                        static_cast<int>(c));
   __syncwarp();
-  if (maxc > 16) {
-    for (int half = 0; half < 2; ++half) {
-      const uint32_t c = half ? c1 : c0;
-      const uint32_t st0 = half ? start1 : start0;
-      unsigned big = __ballot_sync(kFull, lane + 32 * half < B && c > 16);
-      while (big) {
-        const int b = __ffs(big) - 1;
-        big &= big - 1;
-        const int st = static_cast<int>(__shfl_sync(kFull, st0, b));
-        const int cb = static_cast<int>(__shfl_sync(kFull, c, b));
-        warp_bitonic_smem<K, !kVals>(rm, st, cb, lane);
-      }
+  unsigned big = __ballot_sync(kFull, c > 16);
+  while (big) {
+    const int b = __ffs(big) - 1;
+    big &= big - 1;
+    const int st = static_cast<int>(__shfl_sync(kFull, start, b));
+    const int cb = static_cast<int>(__shfl_sync(kFull, c, b));
+    if (cb <= 32) {
+      It y = lane < cb ? rm.get(st + lane) : IO::sentinel(lane);
+      warp_network32(y, lane);
+      __syncwarp();
+      if (lane < cb) rm.set(st + lane, y);
+    } else {
+      warp_bitonic_smem<K, !kVals>(rm, st, cb, lane);
     }
+    __syncwarp();
   }
-  __syncwarp();
 
   // 7. write back (payload gathered by original position)
   if constexpr (kVals) {
@@ -968,7 +993,7 @@ template <class K, bool kVals>
 __global__ void __launch_bounds__(kRssThreads, 2)
     seg_rss_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
                    const Plan* plan, const uint32_t* __restrict__ tile_first, const uint16_t* __restrict__ counts,
-                   const uint16_t* __restrict__ order, unsigned* status) {
+                   const uint16_t* __restrict__ order, int two_min, unsigned* status) {
   using WL = RssWarpLayout<K, kVals>;
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
@@ -1003,7 +1028,8 @@ __global__ void __launch_bounds__(kRssThreads, 2)
     uint32_t* vbuf = reinterpret_cast<uint32_t*>(wbase + WL::kVals_ + b * WL::kValCap);
     const uint32_t ks = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(keys + pe0) & 15) / sizeof(K));
     const uint32_t vs = kVals ? static_cast<uint32_t>((reinterpret_cast<uintptr_t>(vals + pe0) & 15) / 4) : 0u;
-    rss_segment<K, kVals>(kbuf, vbuf, static_cast<int>(ks), static_cast<int>(vs), static_cast<int>(pL), rm, lane);
+    rss_segment<K, kVals>(kbuf, vbuf, static_cast<int>(ks), static_cast<int>(vs), static_cast<int>(pL), rm, lane,
+                          two_min);
     fence_proxy_async_smem();
     __syncwarp();
     store_range<K>(keys, kbuf, ks, pe0, pL, lane);
@@ -1058,6 +1084,38 @@ __global__ void __launch_bounds__(kRssThreads, 2)
 
 // ------------------------------------------------------------ host side ----
 
+constexpr int kCacheDevices = 64;
+constexpr int kCacheTileSizes = 5;  // tile_units 512, 1024, ..., 8192 (powers of two); others are not cached
+
+// Cache entry of a launch shape for device d and tile size E (null: do not cache).
+inline std::atomic<int>* cache_slot(std::atomic<int>* cache, const DeviceInfo& d, uint32_t E) {
+  int t = 0;
+  if (E) {
+    if (E & (E - 1)) return nullptr;
+    t = 31 - __builtin_clz(E) - 9;
+    if (t < 0 || t >= kCacheTileSizes) return nullptr;
+  }
+  if (d.device < 0 || d.device >= kCacheDevices) return nullptr;
+  return &cache[d.device * kCacheTileSizes + t];
+}
+
+// Resident blocks per SM of `kern` with `smem` bytes of dynamic shared
+// memory; the attribute set-up and the occupancy query run once per cache
+// entry (0 = not yet known), so later calls make no runtime queries.
+template <class Kern>
+cudaError_t blocks_per_sm(Kern kern, int threads, int smem, std::atomic<int>* cached, int* out) {
+  int per_sm = cached ? cached->load(std::memory_order_relaxed) : 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+    if (cached) cached->store(per_sm, std::memory_order_relaxed);
+  }
+  *out = per_sm;
+  return cudaSuccess;
+}
+
 template <class K, bool kVals>
 cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, bool rss_only,
                        void* scratch, const SegTuning& tun, cudaStream_t stream, const DeviceInfo& d) {
@@ -1077,20 +1135,18 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const unsigned g2 = static_cast<unsigned>(std::max<uint64_t>(
       1, std::min<uint64_t>(sl.cap - 1, 8ull * d.sm_count)));
-  seg_bin_kernel<<<g2, 256, 0, stream>>>(offsets, plan, tile_first, counts, order, rss_only);
+  seg_bin_kernel<<<g2, 256, 0, stream>>>(offsets, plan, tile_first, counts, order, rss_only,
+                                          tun.net_classes);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   {
     const TileLayout<K, kVals> lay(E);
     const int smem_bytes = static_cast<int>(lay.total);
     auto kern = seg_tile_kernel<K, kVals>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes)) != cudaSuccess)
-      return e;
+    static std::atomic<int> cache[kCacheDevices * kCacheTileSizes];
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem_bytes)) !=
-        cudaSuccess)
+    if ((e = blocks_per_sm(kern, kTileThreads, smem_bytes, cache_slot(cache, d, E), &per_sm)) != cudaSuccess)
       return e;
-    per_sm = std::max(per_sm, 1);
     const unsigned g3 = static_cast<unsigned>(
         std::max<uint64_t>(1, std::min<uint64_t>(sl.cap - 1, static_cast<uint64_t>(d.sm_count) * per_sm)));
     kern<<<g3, kTileThreads, smem_bytes, stream>>>(keys, vals, offsets, plan, tile_first, counts, order, E,
@@ -1101,17 +1157,15 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
     using WL = RssWarpLayout<K, kVals>;
     const int smem_bytes = static_cast<int>(kRssWarps * WL::kBytes);
     auto kern = seg_rss_kernel<K, kVals>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes)) != cudaSuccess)
-      return e;
+    static std::atomic<int> cache[kCacheDevices * kCacheTileSizes];
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRssThreads, smem_bytes)) !=
-        cudaSuccess)
+    if ((e = blocks_per_sm(kern, kRssThreads, smem_bytes, cache_slot(cache, d, 0), &per_sm)) != cudaSuccess)
       return e;
-    per_sm = std::max(per_sm, 1);
     const uint64_t tiles_cap = sl.cap - 1;
     const unsigned g4 = static_cast<unsigned>(std::max<uint64_t>(
         1, std::min<uint64_t>((tiles_cap + kRssWarps - 1) / kRssWarps, static_cast<uint64_t>(d.sm_count) * per_sm)));
-    kern<<<g4, kRssThreads, smem_bytes, stream>>>(keys, vals, offsets, plan, tile_first, counts, order, d.status);
+    kern<<<g4, kRssThreads, smem_bytes, stream>>>(keys, vals, offsets, plan, tile_first, counts, order,
+                                                   tun.rss_two_min, d.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1121,7 +1175,9 @@ template <class K>
 cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,
                             void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
                             const DeviceInfo& d) {
-  if (t.tile_units < 512 || t.tile_units > 8192) return cudaErrorInvalidValue;
+  if (t.tile_units < 512 || t.tile_units > 8192 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg ||
+      t.net_classes > 0xFu)
+    return cudaErrorInvalidValue;
   if (scratch_bytes < ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total) return cudaErrorInvalidValue;
   const bool rss = mode == SegMode::kRssOnly;
   return vals ? launch_all<K, true>(keys, vals, offsets, nseg, rss, scratch, t, s, d)
