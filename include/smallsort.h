@@ -126,6 +126,49 @@ int sn_sort_segments_u64_noalloc(uint64_t *keys, uint32_t *vals, const uint32_t 
                                  uint64_t nseg, sn_stream_t stream);
 
 /*
+ * Launch parameters of the segmented calls, and their autotuner.  (Library
+ * addition: the paper's CPU sorters have no launch parameters.)  Each device
+ * keeps one parameter set per key type and payload kind (u32 / u64 keys,
+ * with / without payload); sn_sort_segments*, rss_sort_segments* and the
+ * request server read it at every call.  Parameters change speed only, never
+ * results.
+ */
+typedef struct {
+    int tile_units;        /* segments + items per tile of the network kernel: 512..8192 (default 2048);
+                              at most 4096 unless keys are u32 without payload (shared memory) */
+    unsigned net_classes;  /* padded network sizes for 2..16-item segments: bit 0 = 2, bit 1 = 4,
+                              bit 2 = 8, bit 3 = 12 channels; 16 channels always (default 0xF) */
+    int rss_two_min;       /* Register Sample Sort: segments longer than this draw a 64-item sample,
+                              shorter ones 32 (16..256, default 160) */
+} sn_tuning;
+
+/* Current parameters of the current device for (key_bytes = 4 or 8, with_vals = 0 or 1). */
+int sn_tuning_get(int key_bytes, int with_vals, sn_tuning *out);
+/* Installs parameters (SN_EINVAL if out of range). */
+int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning *t);
+/*
+ * Autotuner: times sn_sort_segments on the caller's batch (device pointers,
+ * same contract as sn_sort_segments / _u64 with key_bytes 4 / 8) under
+ * candidate parameters -- a coordinate search over net_classes, tile_units
+ * and rss_two_min, best of three runs each, the input restored from a device
+ * copy before every run -- installs the fastest set for this key type and
+ * payload kind on the current device and copies it to `out` (may be NULL).
+ * Synchronous: returns after the search; the batch is left sorted.
+ * Needs device memory for one copy of keys and payload (SN_ENOMEM if not).
+ * `best_ms`, if not NULL, receives the time of one sort with the chosen set.
+ */
+int sn_tune_segments(void *keys, uint32_t *vals, const uint32_t *offsets, uint64_t nseg, int key_bytes,
+                     sn_stream_t stream, sn_tuning *out, float *best_ms);
+/*
+ * Writes every parameter set that was set or tuned in this process to a text
+ * file (one line per device, key type and payload kind), and reads such a file
+ * back, installing the sets of devices present.  SN_EINVAL on I/O or format
+ * errors.
+ */
+int sn_tuning_save(const char *path);
+int sn_tuning_load(const char *path);
+
+/*
  * Synchronises `stream`, then returns and clears the device status word of the
  * current device: SN_ERANGE if a segmented call met bad offsets, SN_ETIMEOUT
  * if a bounded device wait ran out, SN_ECUDA if the stream reported a CUDA

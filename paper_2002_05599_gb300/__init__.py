@@ -19,6 +19,7 @@ from ._binding import (  # noqa: F401
     SN_EUNSUPPORTED,
     SN_OK,
     SmallSortError,
+    SnTuning,
     check,
     library,
     library_path,
@@ -30,4 +31,9 @@ from ._binding import (  # noqa: F401
     sn_sort_segments,
     sn_sort_segments_u64,
     sn_status_string,
+    sn_tune_segments,
+    sn_tuning_get,
+    sn_tuning_load,
+    sn_tuning_save,
+    sn_tuning_set,
 )

@@ -125,6 +125,60 @@ def rss_sort_segments_u64(keys, vals, offsets, nseg: int | None = None, stream=N
     return _segments(library().rss_sort_segments_u64, 8, keys, vals, offsets, nseg, stream)
 
 
+class SnTuning(ctypes.Structure):
+    _fields_ = [("tile_units", ctypes.c_int), ("net_classes", ctypes.c_uint), ("rss_two_min", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {"tile_units": self.tile_units, "net_classes": self.net_classes, "rss_two_min": self.rss_two_min}
+
+
+def _tune_lib():
+    lib = library()
+    if not getattr(lib, "_tune_bound", False):
+        P = ctypes.c_void_p
+        lib.sn_tuning_get.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SnTuning)]
+        lib.sn_tuning_set.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SnTuning)]
+        lib.sn_tune_segments.argtypes = [P, P, P, ctypes.c_uint64, ctypes.c_int, P, ctypes.POINTER(SnTuning),
+                                         ctypes.POINTER(ctypes.c_float)]
+        lib.sn_tuning_save.argtypes = [ctypes.c_char_p]
+        lib.sn_tuning_load.argtypes = [ctypes.c_char_p]
+        for name in ("sn_tuning_get", "sn_tuning_set", "sn_tune_segments", "sn_tuning_save", "sn_tuning_load"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib._tune_bound = True
+    return lib
+
+
+def sn_tuning_get(key_bytes: int, with_vals: bool) -> dict:
+    t = SnTuning()
+    check(_tune_lib().sn_tuning_get(key_bytes, int(with_vals), ctypes.byref(t)), "sn_tuning_get")
+    return t.as_dict()
+
+
+def sn_tuning_set(key_bytes: int, with_vals: bool, tile_units: int = 2048, net_classes: int = 0xF,
+                  rss_two_min: int = 160) -> int:
+    t = SnTuning(tile_units, net_classes, rss_two_min)
+    return _tune_lib().sn_tuning_set(key_bytes, int(with_vals), ctypes.byref(t))
+
+
+def sn_tune_segments(keys, vals, offsets, nseg: int | None = None, stream=None):
+    """Autotune the segmented call on this batch; returns (parameters, ms of one sort)."""
+    if nseg is None:
+        nseg = _elems(offsets, 4) - 1
+    kb = keys.element_size()
+    t, ms = SnTuning(), ctypes.c_float()
+    check(_tune_lib().sn_tune_segments(_addr(keys), _addr(vals), _addr(offsets), nseg, kb, _stream(stream),
+                                       ctypes.byref(t), ctypes.byref(ms)), "sn_tune_segments")
+    return t.as_dict(), float(ms.value)
+
+
+def sn_tuning_save(path: str) -> int:
+    return _tune_lib().sn_tuning_save(os.fsencode(path))
+
+
+def sn_tuning_load(path: str) -> int:
+    return _tune_lib().sn_tuning_load(os.fsencode(path))
+
+
 def sn_check(stream=None) -> int:
     """Synchronise the stream; return and clear the device status word."""
     return library().sn_check(_stream(stream))

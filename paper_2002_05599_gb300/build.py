@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsmallsort.so")
-SOURCES = ["sn_api.cu", "sn_fixed.cu", "sn_segments_u32.cu", "sn_segments_u64.cu"]
+SOURCES = ["sn_api.cu", "sn_fixed.cu", "sn_segments_u32.cu", "sn_segments_u64.cu", "sn_server.cu", "sn_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-I", INCLUDE, "-I", CSRC]

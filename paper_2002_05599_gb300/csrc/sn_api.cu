@@ -106,10 +106,20 @@ int segments_entry(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t ns
   const sn::DeviceInfo* d = sn::device_info(&err);
   if (d == nullptr) return err;
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  sn::SegTuning tun;
+  const sn::SegTuning tun = sn::current_tuning(d->device, static_cast<int>(sizeof(K)), vals != nullptr);
   const size_t bytes = sn::segments_scratch_bytes(nseg, tun);
   void* scratch = nullptr;
-  if (cudaMallocFromPoolAsync(&scratch, bytes, d->pool, s) != cudaSuccess) {
+  // Under stream capture the scratch comes from the device's default pool, so
+  // that the graph records an allocation node it owns; otherwise from the
+  // library's pool, which keeps freed scratch for the next call.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return SN_ECUDA;
+  }
+  const cudaError_t ae = cap == cudaStreamCaptureStatusActive ? cudaMallocAsync(&scratch, bytes, s)
+                                                              : cudaMallocFromPoolAsync(&scratch, bytes, d->pool, s);
+  if (ae != cudaSuccess) {
     cudaGetLastError();
     return SN_ENOMEM;
   }

@@ -31,6 +31,18 @@ struct SegTuning {
   int rss_two_min = 160;       // RSS segments longer than this take a 64-item sample, else 32 (16..256)
 };
 
+// Parameters installed for (device, key bytes, payload) (sn_tune.cu); the
+// defaults until sn_tuning_set / sn_tune_segments / sn_tuning_load.
+SegTuning current_tuning(int device, int key_bytes, bool vals);
+bool tuning_valid(const SegTuning& t);
+
+// Largest tile_units whose staging fits in shared memory (sn_segments_*.cu).
+int max_tile_units_u32(bool vals);
+int max_tile_units_u64(bool vals);
+inline int max_tile_units(int key_bytes, bool vals) {
+  return key_bytes == 8 ? max_tile_units_u64(vals) : max_tile_units_u32(vals);
+}
+
 // Device scratch needed for a segmented call with nseg segments.
 size_t segments_scratch_bytes(uint64_t nseg, const SegTuning& t);
 

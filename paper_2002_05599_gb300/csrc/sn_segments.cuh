@@ -1099,14 +1099,28 @@ inline std::atomic<int>* cache_slot(std::atomic<int>* cache, const DeviceInfo& d
   return &cache[d.device * kCacheTileSizes + t];
 }
 
+// Dynamic shared memory a tile-kernel block may take (the 227 KB per-block
+// limit less a margin for the kernel's static shared memory).
+constexpr size_t kTileSmemLimit = 232448 - 4096;
+
+// Largest power-of-two tile size (512..8192) whose two stages fit.
+template <class K, bool kVals>
+int max_tile_units_for() {
+  for (uint32_t E = 8192; E >= 512; E >>= 1)
+    if (TileLayout<K, kVals>(E).total <= kTileSmemLimit) return static_cast<int>(E);
+  return 0;
+}
+
 // Resident blocks per SM of `kern` with `smem` bytes of dynamic shared
-// memory; the attribute set-up and the occupancy query run once per cache
-// entry (0 = not yet known), so later calls make no runtime queries.
+// memory; the attribute set-up (to `attr_smem`, the most any launch of the
+// kernel uses, so that one launch's set-up never lowers another's limit) and
+// the occupancy query run once per cache entry (0 = not yet known), so later
+// calls make no runtime queries.
 template <class Kern>
-cudaError_t blocks_per_sm(Kern kern, int threads, int smem, std::atomic<int>* cached, int* out) {
+cudaError_t blocks_per_sm(Kern kern, int threads, int smem, int attr_smem, std::atomic<int>* cached, int* out) {
   int per_sm = cached ? cached->load(std::memory_order_relaxed) : 0;
   if (per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, attr_smem);
     if (e != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
     per_sm = std::max(per_sm, 1);
@@ -1145,7 +1159,8 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
     auto kern = seg_tile_kernel<K, kVals>;
     static std::atomic<int> cache[kCacheDevices * kCacheTileSizes];
     int per_sm = 0;
-    if ((e = blocks_per_sm(kern, kTileThreads, smem_bytes, cache_slot(cache, d, E), &per_sm)) != cudaSuccess)
+    const int attr = static_cast<int>(TileLayout<K, kVals>(max_tile_units_for<K, kVals>()).total);
+    if ((e = blocks_per_sm(kern, kTileThreads, smem_bytes, attr, cache_slot(cache, d, E), &per_sm)) != cudaSuccess)
       return e;
     const unsigned g3 = static_cast<unsigned>(
         std::max<uint64_t>(1, std::min<uint64_t>(sl.cap - 1, static_cast<uint64_t>(d.sm_count) * per_sm)));
@@ -1159,7 +1174,8 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
     auto kern = seg_rss_kernel<K, kVals>;
     static std::atomic<int> cache[kCacheDevices * kCacheTileSizes];
     int per_sm = 0;
-    if ((e = blocks_per_sm(kern, kRssThreads, smem_bytes, cache_slot(cache, d, 0), &per_sm)) != cudaSuccess)
+    if ((e = blocks_per_sm(kern, kRssThreads, smem_bytes, smem_bytes, cache_slot(cache, d, 0), &per_sm)) !=
+        cudaSuccess)
       return e;
     const uint64_t tiles_cap = sl.cap - 1;
     const unsigned g4 = static_cast<unsigned>(std::max<uint64_t>(
@@ -1175,8 +1191,9 @@ template <class K>
 cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,
                             void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
                             const DeviceInfo& d) {
-  if (t.tile_units < 512 || t.tile_units > 8192 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg ||
-      t.net_classes > 0xFu)
+  if (t.tile_units < 512 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg || t.net_classes > 0xFu)
+    return cudaErrorInvalidValue;
+  if (t.tile_units > (vals ? max_tile_units_for<K, true>() : max_tile_units_for<K, false>()))
     return cudaErrorInvalidValue;
   if (scratch_bytes < ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total) return cudaErrorInvalidValue;
   const bool rss = mode == SegMode::kRssOnly;

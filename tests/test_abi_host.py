@@ -85,3 +85,59 @@ def test_no_gpu_is_a_clean_error(lib):
     fn = lib.sn_sort_fixed
     fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p]
     assert fn(0x1000, 8, 10, None) in (-4, -6)
+
+
+def test_server_argument_errors(lib):
+    from paper_2002_05599_gb300.server import ServerConfig
+    P = ctypes.c_void_p
+    create = lib.sn_server_create
+    create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
+    h = P()
+    assert create(None, ctypes.byref(h)) == -1
+    for bad in (ServerConfig(1 << 20, 2, 4, 0, 0, 0),       # key_bytes not 4 or 8
+                ServerConfig(1 << 20, 4, 17, 0, 0, 0),      # too many slots
+                ServerConfig(1 << 20, 4, 4, 1 << 40, 0, 0),  # batch key limit above 2^31
+                ServerConfig(1 << 20, 4, 4, 0, 0, 100000),  # too many requests per batch
+                ServerConfig(16, 4, 4, 0, 0, 0)):           # budget below one allocation unit
+        assert create(ctypes.byref(bad), ctypes.byref(h)) == -1
+        assert not h.value
+    submit = lib.sn_server_submit
+    submit.argtypes = [P, P, P, P, ctypes.c_uint64, P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
+    t = ctypes.c_uint64()
+    assert submit(None, None, None, None, 0, None, None, 0, ctypes.byref(t)) == -1
+    for name in ("sn_server_drain", "sn_server_destroy"):
+        getattr(lib, name).argtypes = [P]
+        assert getattr(lib, name)(None) == -1
+    lib.sn_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int64]
+    assert lib.sn_server_wait(None, 1, 0) == -1
+    import torch
+    if not torch.cuda.is_available():  # a valid config still needs the GPU
+        assert create(ctypes.byref(ServerConfig(1 << 20, 4, 4, 0, 0, 0)), ctypes.byref(h)) in (-4, -6)
+
+
+def test_tuning_argument_errors_and_file_format(lib, tmp_path):
+    import paper_2002_05599_gb300 as sn
+    from paper_2002_05599_gb300._binding import SnTuning
+    L = sn._binding._tune_lib()
+    t = SnTuning(2048, 0xF, 160)
+    assert L.sn_tuning_set(2, 0, ctypes.byref(t)) == -1            # key_bytes
+    assert L.sn_tuning_get(4, 0, None) == -1
+    for bad in (SnTuning(256, 0xF, 160), SnTuning(16384, 0xF, 160), SnTuning(2048, 0x10, 160),
+                SnTuning(2048, 0xF, 8), SnTuning(2048, 0xF, 300)):
+        assert L.sn_tuning_set(4, 1, ctypes.byref(bad)) == -1
+    L.sn_tune_segments.argtypes = L.sn_tune_segments.argtypes
+    assert L.sn_tune_segments(None, None, None, 5, 4, None, None, None) == -1
+    assert L.sn_tune_segments(0x1000, None, 0x2000, 5, 3, None, None, None) == -1
+    assert sn.sn_tuning_save(os.path.join(tmp_path, "no", "such", "dir.txt")) == -1
+    bad_file = os.path.join(tmp_path, "bad.txt")
+    with open(bad_file, "w") as f:
+        f.write("smallsort-tuning 1\n0 4 0 2048 15\n")  # truncated line
+    assert sn.sn_tuning_load(bad_file) == -1
+    with open(bad_file, "w") as f:
+        f.write("smallsort-tuning 1\n0 4 0 100 15 160\n")  # tile size out of range
+    assert sn.sn_tuning_load(bad_file) == -1
+    assert sn.sn_tuning_load(os.path.join(tmp_path, "missing.txt")) == -1
+    good = os.path.join(tmp_path, "good.txt")
+    with open(good, "w") as f:
+        f.write("smallsort-tuning 1\n0 4 0 4096 5 128\n0 8 1 1024 15 192\n")
+    assert sn.sn_tuning_load(good) == 0  # entries for devices that are not present are skipped

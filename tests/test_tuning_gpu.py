@@ -1,0 +1,75 @@
+"""Launch parameters change speed only: every parameter set sorts a batch to
+the oracle's result, and the autotuner leaves the batch sorted and installs
+the set it reports."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2002_05599_gb300 as sn
+from paper_2002_05599_gb300 import workloads as wl
+from gpu_util import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+SETS = [dict(tile_units=512, net_classes=0x0, rss_two_min=16),
+        dict(tile_units=4096, net_classes=0xF, rss_two_min=256),
+        dict(tile_units=1024, net_classes=0x5, rss_two_min=64),
+        dict(tile_units=4096, net_classes=0xA, rss_two_min=200)]
+
+
+@pytest.fixture
+def restore_defaults():
+    yield
+    for kb in (4, 8):
+        for v in (False, True):
+            sn.check(sn.sn_tuning_set(kb, v), "defaults")
+
+
+@pytest.mark.parametrize("dtype,with_vals", [(np.uint64, True), (np.uint32, False), (np.uint32, True)])
+def test_every_parameter_set_gives_the_same_result(dtype, with_vals, restore_defaults):
+    kb = np.dtype(dtype).itemsize
+    fn = sn.sn_sort_segments_u64 if kb == 8 else sn.sn_sort_segments
+    rss = sn.rss_sort_segments_u64 if kb == 8 else sn.rss_sort_segments
+    k, v, off = wl.segment_batch(60_000, "uniform", "fewdistinct", dtype, with_vals, seed=77, lo=0, hi=256)
+    ek, ev = oracle.sort_segments(k, v, off)
+    d_off = to_dev(off)
+    for params in SETS:
+        sn.check(sn.sn_tuning_set(kb, with_vals, **params), "set")
+        assert sn.sn_tuning_get(kb, with_vals) == params
+        for call in (fn, rss):
+            dk = to_dev(k)
+            dv = to_dev(v) if with_vals else None
+            sn.check(call(dk, dv, d_off), "sort")
+            assert sn.sn_check() == sn.SN_OK
+            assert np.array_equal(to_host(dk, dtype), ek), params
+            if with_vals:
+                assert np.array_equal(to_host(dv, np.uint32), ev), params
+
+
+def test_tile_size_limit_by_shared_memory(restore_defaults):
+    # two stages of 8192-unit tiles fit in shared memory only for u32 keys without payload
+    assert sn.sn_tuning_set(4, False, tile_units=8192) == sn.SN_OK
+    for kb, v in ((4, True), (8, False), (8, True)):
+        assert sn.sn_tuning_set(kb, v, tile_units=8192) == sn.SN_EINVAL
+        assert sn.sn_tuning_set(kb, v, tile_units=4096) == sn.SN_OK
+    k, _, off = wl.segment_batch(50_000, "geometric", "uniform", np.uint32, False, seed=79, p=0.15, cap=256)
+    dk = to_dev(k)
+    sn.check(sn.sn_tuning_set(4, False, tile_units=8192), "set")
+    sn.check(sn.sn_sort_segments(dk, None, to_dev(off)), "sort")
+    assert sn.sn_check() == sn.SN_OK
+    assert np.array_equal(to_host(dk, np.uint32), oracle.sort_segments(k, None, off)[0])
+
+
+def test_autotuner_installs_its_choice_and_sorts(tmp_path, restore_defaults):
+    k, v, off = wl.segment_batch(1 << 18, "geometric", "uniform", np.uint64, True, seed=78, p=0.15, cap=256)
+    ek, ev = oracle.sort_segments(k, v, off)
+    dk, dv, d_off = to_dev(k), to_dev(v), to_dev(off)
+    params, ms = sn.sn_tune_segments(dk, dv, d_off)
+    assert ms > 0
+    assert sn.sn_tuning_get(8, True) == params
+    assert np.array_equal(to_host(dk, np.uint64), ek) and np.array_equal(to_host(dv, np.uint32), ev)
+    path = str(tmp_path / "tuning.txt")
+    assert sn.sn_tuning_save(path) == sn.SN_OK
+    sn.check(sn.sn_tuning_set(8, True), "reset")
+    assert sn.sn_tuning_load(path) == sn.SN_OK
+    assert sn.sn_tuning_get(8, True) == params
