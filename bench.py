@@ -60,6 +60,12 @@ def parse_args():
                     help="comma-separated subset of sweep,uneven,rss (profiling only; default all)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="call the uneven batch directly instead of replaying its captured CUDA graph")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-vs-batched comparison")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving loop")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson request stream")
+    ap.add_argument("--serve-rate", type=float, default=20000.0, help="mean request arrival rate (1/s)")
     return ap.parse_args()
 
 
@@ -202,8 +208,9 @@ def launches_per_step(parts=("sweep", "uneven", "rss")):
 PARTS = ("sweep", "uneven", "rss")
 
 
-def run_parts(sn, w, events=None, parts=PARTS):
-    """One step on the current stream; events[0..3] bracket sweep / uneven / rss."""
+def run_parts(sn, w, events=None, parts=PARTS, graphs=None):
+    """One step on the current stream; events[0..3] bracket sweep / uneven / rss.
+    graphs["uneven"], when given, is the captured uneven-batch call."""
     if events:
         events[0].record()
     if "sweep" in parts:
@@ -212,7 +219,10 @@ def run_parts(sn, w, events=None, parts=PARTS):
     if events:
         events[1].record()
     if "uneven" in parts:
-        sn.check(sn.sn_sort_segments_u64(w["uneven_keys"], w["uneven_vals"], w["uneven_off"]), "uneven")
+        if graphs and "uneven" in graphs:
+            graphs["uneven"].replay()
+        else:
+            sn.check(sn.sn_sort_segments_u64(w["uneven_keys"], w["uneven_vals"], w["uneven_off"]), "uneven")
     if events:
         events[2].record()
     if "rss" in parts:
@@ -246,6 +256,13 @@ def bench_ours(args, rank, world, local_rank, dist):
     torch.cuda.synchronize()
     status = sn.sn_check()
     sn.check(status, "warm-up")
+    graphs = {}
+    if "uneven" in parts and not args.no_graph:
+        graphs["uneven"] = capture_uneven(sn, work)
+        restore()
+        run_parts(sn, work, parts=("uneven",), graphs=graphs)
+        torch.cuda.synchronize()
+        sn.check(sn.sn_check(), "graph warm-up")
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     sampler = ClockSampler(local_rank) if rank == 0 else None
@@ -258,7 +275,7 @@ def bench_ours(args, rank, world, local_rank, dist):
     t0 = time.perf_counter()
     for k in range(args.steps):
         restore()
-        run_parts(sn, work, ev[k], parts=parts)
+        run_parts(sn, work, ev[k], parts=parts, graphs=graphs)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clocks = sampler.stop() if sampler else None
@@ -312,16 +329,232 @@ def bench_ours(args, rank, world, local_rank, dist):
         "wall_s_timed_loop": round(wall, 3),
     }
 
+    result["config"]["uneven_launch"] = ("replay of a captured CUDA graph (plan memset, plan / bin / tile / RSS "
+                                         "kernels, scratch allocation nodes)" if graphs else "direct call")
     if not args.no_e2e:
         result["e2e"] = bench_e2e(args, sn, pristine, world, dist, device, parts)
-    del work
+    del work, graphs
+    if not args.no_plain:
+        result["plain_vs_batched"] = bench_plain_vs_batched(args, sn, device, dist)
+    if rank == 0 and world == 1 and not args.no_serving:
+        result["serving"] = bench_serving(args, device)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(sizes, budget_s=12.0)
     return result
 
 
+def capture_uneven(sn, w):
+    """The uneven-batch call captured once into a CUDA graph (same buffers every step)."""
+    import torch
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        sn.check(sn.sn_sort_segments_u64(w["uneven_keys"], w["uneven_vals"], w["uneven_off"]), "capture")
+    torch.cuda.current_stream().wait_stream(stream)
+    return graph
+
+
+# ------------------------------------------------- plain vs batched ---------
+
+def bench_plain_vs_batched(args, sn, device, dist):
+    """The same arrays sorted two ways: plain = grouped by length into
+    contiguous fixed-n arrays, one sn_sort_fixed launch per n; batched = the
+    CSR batch in its original interleaved order, one sn_sort_segments call.
+    Lengths uniform 1..16 (length-1 segments need no work in either form)."""
+    import torch
+    from paper_2002_05599_gb300 import workloads as wl
+    nseg = (1 << 24) >> args.scale
+    out = {"workload": f"{nseg} segments, lengths uniform 1..16, keys only, uniform keys (seed 3)",
+           "timing": "CUDA events per call sequence, mean of the timed repetitions; "
+                     "inputs restored from pristine copies between repetitions"}
+    lens = wl.segment_lengths(nseg, "uniform", seed=3, lo=1, hi=16)
+    off = wl.offsets_from_lengths(lens)
+    total = int(off[-1])
+    d_off = torch.from_numpy(off.view(np.int32)).to(device)
+    # plain layout: segments stably grouped by length (built once, untimed)
+    order = np.argsort(lens, kind="stable")
+    starts = off[:-1][order].astype(np.int64)
+    glens = lens[order].astype(np.int64)
+    gather = np.repeat(starts, glens) + (np.arange(total) - np.repeat(np.cumsum(glens) - glens, glens))
+    d_gather = torch.from_numpy(gather).to(device)
+    counts = np.bincount(lens, minlength=17)
+    for dtype, name, fixed, seg in ((np.uint64, "u64", sn.sn_sort_fixed_u64, sn.sn_sort_segments_u64),
+                                    (np.uint32, "u32", sn.sn_sort_fixed, sn.sn_sort_segments)):
+        keys = wl.uniform_keys_torch(total, dtype, seed=3, device=device)
+        grouped = keys[d_gather].contiguous()
+        work_b, work_p = keys.clone(), grouped.clone()
+        views, at = {}, 0
+        for n in range(1, 17):
+            views[n] = work_p[at:at + counts[n] * n]
+            at += counts[n] * n
+
+        def plain():
+            for n in range(2, 17):
+                if counts[n]:
+                    sn.check(fixed(views[n], n, int(counts[n])), f"plain n={n}")
+
+        def batched():
+            sn.check(seg(work_b, None, d_off), "batched")
+
+        res = {}
+        for label, fn, src, dst in (("plain", plain, grouped, work_p), ("batched", batched, keys, work_b)):
+            for _ in range(max(3, args.warmup)):
+                dst.copy_(src)
+                fn()
+            times = []
+            for _ in range(max(3, args.steps)):
+                dst.copy_(src)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                b.synchronize()
+                times.append(a.elapsed_time(b))
+            res[label] = statistics.mean(times)
+        sn.check(sn.sn_check(), "plain vs batched")
+        # both forms sorted the same arrays: compare through the grouping
+        assert torch.equal(work_b[d_gather], work_p), "plain and batched results differ"
+        ms_p, ms_b = res["plain"], res["batched"]
+        if dist:
+            t = torch.tensor([ms_p, ms_b], dtype=torch.float64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_p, ms_b = t.tolist()
+        out[name] = {"plain_ms": round(ms_p, 4), "plain_gkeys_s": round(total / (ms_p * 1e-3) / 1e9, 2),
+                     "plain_launches": int(sum(1 for n in range(2, 17) if counts[n])),
+                     "batched_ms": round(ms_b, 4), "batched_gkeys_s": round(total / (ms_b * 1e-3) / 1e9, 2),
+                     "batched_launches": 4, "batched_over_plain": round(ms_p / ms_b, 3)}
+        del keys, grouped, work_b, work_p, views
+    return out
+
+
+# ----------------------------------------------------------- serving --------
+
+def bench_serving(args, device):
+    """Continuous batching under a Poisson request stream: requests of
+    log-uniform 1..10^5 segments (lengths uniform 2..256, u32 uniform keys) in
+    pinned host memory, served by the library's request server under a 40 GB
+    device budget; latency = arrival -> sorted keys back in host memory."""
+    import ctypes
+    import torch
+    from paper_2002_05599_gb300 import workloads as wl
+    from paper_2002_05599_gb300.server import SortServer, _lib, now_ns
+    pool_nseg = (1 << 22) >> args.scale
+    lens = wl.segment_lengths(pool_nseg, "uniform", seed=7, lo=2, hi=256)
+    off = wl.offsets_from_lengths(lens)
+    total = int(off[-1])
+    keys_in = torch.empty(total, dtype=torch.int32, pin_memory=True)
+    keys_in.copy_(wl.uniform_keys_torch(total, np.uint32, seed=7, device=device))
+    keys_out = torch.empty(total, dtype=torch.int32, pin_memory=True)
+    off_h = torch.from_numpy(off.view(np.int32)).pin_memory()
+    rng = np.random.default_rng(1)
+    n_req = max(1, int(args.serve_rate * args.serve_seconds))
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, n_req))
+    max_cnt = min(100_000, pool_nseg)
+    counts = np.floor(np.exp(rng.uniform(0.0, np.log(max_cnt + 1), n_req))).astype(np.int64).clip(1, max_cnt)
+    starts = rng.integers(0, pool_nseg - counts + 1)
+    budget = 40 << 30
+    srv = SortServer(budget_bytes=budget, key_bytes=4, slots=4)
+    lib, h = _lib(), srv._h
+    kin, kout, offp = keys_in.data_ptr(), keys_out.data_ptr(), off_h.data_ptr()
+    ticket = ctypes.c_uint64()
+
+    def stream(n, t0):
+        lag = 0
+        for i in range(n):
+            due = t0 + int(arrivals[i] * 1e9)
+            while now_ns() < due:
+                pass
+            lag = max(lag, now_ns() - due)
+            rc = lib.sn_server_submit(h, kin, None, offp + 4 * int(starts[i]), int(counts[i]), kout, None, due,
+                                      ctypes.byref(ticket))
+            if rc != 0:
+                raise RuntimeError(f"submit failed: {rc}")
+        srv.drain()
+        return lag
+
+    stream(min(n_req, 200), now_ns() + 1_000_000)  # warm-up: device set-up, first batches
+    srv.stats(reset=True)
+    lag = stream(n_req, now_ns() + 2_000_000)
+    st = srv.stats()
+    srv.close()
+    keys_req = float(np.sum(off[starts + counts].astype(np.int64) - off[starts].astype(np.int64)))
+    span = float(arrivals[-1])
+    return {"requests": n_req, "rate_hz": args.serve_rate, "seconds": round(span, 3),
+            "segments_per_request": "log-uniform 1..1e5", "segment_lengths": "uniform 2..256",
+            "keys": "u32 uniform, pinned host memory", "budget_gb": budget / 2**30, "slots": 4,
+            "offered_gkeys_s": round(keys_req / span / 1e9, 2),
+            "achieved_gkeys_s": round(st["keys_per_s"] / 1e9, 2),
+            "p50_ms": round(st["latency_p50_us"] / 1e3, 3), "p99_ms": round(st["latency_p99_us"] / 1e3, 3),
+            "max_ms": round(st["latency_max_us"] / 1e3, 3), "mean_ms": round(st["latency_mean_us"] / 1e3, 3),
+            "completed": st["completed"], "failed": st["failed"], "batches": st["batches"],
+            "max_requests_per_batch": st["max_batch_requests_seen"], "max_batches_in_flight": st["max_inflight_seen"],
+            "peak_device_gb": round(st["peak_device_bytes"] / 2**30, 3), "client_max_lag_ms": round(lag / 1e6, 3)}
+
+
+def e2e_jobs(sn, host, out, dev, parts):
+    """The step cut into jobs of (host->device copies, sorts, device->host
+    copies): one per fixed n, the uneven batch in 4 and the RSS range in 2
+    contiguous segment ranges (offsets stay absolute: a range is sorted by
+    passing the offsets from its first segment)."""
+    jobs = []
+    if "sweep" in parts:
+        for n in SWEEP_NS:
+            k = f"sweep{n}"
+            jobs.append(([(host[k], dev[k])], lambda s, k=k, n=n: sn.check(sn.sn_sort_fixed(dev[k], n, stream=s)),
+                         [(dev[k], out[k])]))
+    for part, nchunks, fn in (("uneven", 4, sn.sn_sort_segments_u64), ("rss", 2, sn.rss_sort_segments)):
+        if part not in parts:
+            continue
+        off_h = host[f"{part}_off"].numpy().view(np.uint32)
+        nseg = off_h.size - 1
+        keys, vals = f"{part}_keys", f"{part}_vals"
+        for c in range(nchunks):
+            a, b = nseg * c // nchunks, nseg * (c + 1) // nchunks
+            ea, eb = int(off_h[a]), int(off_h[b])
+            h2d = [(host[f"{part}_off"][a:b + 1], dev[f"{part}_off"][a:b + 1]),
+                   (host[keys][ea:eb], dev[keys][ea:eb])]
+            d2h = [(dev[keys][ea:eb], out[keys][ea:eb])]
+            if vals in host:
+                h2d.append((host[vals][ea:eb], dev[vals][ea:eb]))
+                d2h.append((dev[vals][ea:eb], out[vals][ea:eb]))
+
+            def run(s, a=a, b=b, keys=keys, vals=vals, fn=fn, part=part):
+                sn.check(fn(dev[keys], dev.get(vals), dev[f"{part}_off"][a:b + 1], b - a, stream=s), part)
+            jobs.append((h2d, run, d2h))
+    return jobs
+
+
+def e2e_check(host, out, parts, samples=2000):
+    """Spot check of the pipelined results on the host: sampled arrays and
+    segments must equal numpy's sort of the same input."""
+    rng = np.random.default_rng(5)
+    u = {4: np.uint32, 8: np.uint64}
+    if "sweep" in parts:
+        for n in SWEEP_NS:
+            k = f"sweep{n}"
+            src = host[k].numpy().view(u[host[k].element_size()]).reshape(-1, n)
+            got = out[k].numpy().view(u[out[k].element_size()]).reshape(-1, n)
+            rows = rng.integers(0, src.shape[0], samples)
+            if not np.array_equal(np.sort(src[rows], axis=1), got[rows]):
+                raise RuntimeError(f"e2e result differs for n={n}")
+    for part in ("uneven", "rss"):
+        if part not in parts:
+            continue
+        off = host[f"{part}_off"].numpy().view(np.uint32)
+        kk = f"{part}_keys"
+        src = host[kk].numpy().view(u[host[kk].element_size()])
+        got = out[kk].numpy().view(u[out[kk].element_size()])
+        for i in rng.integers(0, off.size - 1, samples):
+            a, b = int(off[i]), int(off[i + 1])
+            if not np.array_equal(np.sort(src[a:b]), got[a:b]):
+                raise RuntimeError(f"e2e result differs in {part} segment {i}")
+
+
 def bench_e2e(args, sn, pristine, world, dist, device, parts=PARTS):
-    """The same step through the C ABI with host buffers (pinned)."""
+    """The same step through the C ABI with host buffers (pinned): per job,
+    host->device copies on one stream, the sorts on a second, device->host
+    copies on a third, so the copies of one job overlap the sorts of another."""
     import torch
     host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in pristine.items()}
     for k, v in pristine.items():
@@ -331,16 +564,25 @@ def bench_e2e(args, sn, pristine, world, dist, device, parts=PARTS):
     h2d = sum(t.numel() * t.element_size() for t in host.values())
     d2h = sum(t.numel() * t.element_size() for t in out.values())
     keys = sum(part_keys(pristine).values())
+    jobs = e2e_jobs(sn, host, out, dev, parts)
+    s_h, s_c, s_d = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
 
     def step():
-        for k, v in host.items():
-            dev[k].copy_(v, non_blocking=True)
-        run_parts(sn, dev, parts=parts)
-        for k, v in out.items():
-            v.copy_(dev[k], non_blocking=True)
+        s_h.wait_stream(s_d)  # the previous step's results are out before buffers are refilled
+        for hd, run, dh in jobs:
+            with torch.cuda.stream(s_h):
+                for src, dst in hd:
+                    dst.copy_(src, non_blocking=True)
+            s_c.wait_stream(s_h)
+            run(s_c)
+            s_d.wait_stream(s_c)
+            with torch.cuda.stream(s_d):
+                for src, dst in dh:
+                    dst.copy_(src, non_blocking=True)
 
     step()
     torch.cuda.synchronize()
+    e2e_check(host, out, parts)
     steps = max(1, min(args.steps, 5))
     if dist:
         dist.barrier()
@@ -356,7 +598,8 @@ def bench_e2e(args, sn, pristine, world, dist, device, parts=PARTS):
         sec = float(t.item())
     sn.check(sn.sn_check(), "e2e")
     return {"value": round(world * keys / sec / 1e9, 3), "unit": "Gkeys/s", "ms_per_step": round(sec * 1e3, 3),
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "pipeline": f"{len(jobs)} jobs; H2D, sorts and D2H on three streams"}
 
 
 # ----------------------------------------------------------- CPU oracle -----
