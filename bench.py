@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--no-graph", action="store_true",
                     help="call the uneven batch directly instead of replaying its captured CUDA graph")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-vs-batched comparison")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch parameters instead of autotuning each segmented workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving loop")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson request stream")
     ap.add_argument("--serve-rate", type=float, default=20000.0, help="mean request arrival rate (1/s)")
@@ -256,6 +258,12 @@ def bench_ours(args, rank, world, local_rank, dist):
     torch.cuda.synchronize()
     status = sn.sn_check()
     sn.check(status, "warm-up")
+    tuned = {}
+    if not args.no_tune:  # autotune each segmented workload on its own batch (untimed)
+        if "uneven" in parts:
+            tuned["uneven"] = autotune(sn, work["uneven_keys"], work["uneven_vals"], work["uneven_off"])
+        if "rss" in parts:
+            tuned["rss"] = autotune(sn, work["rss_keys"], None, work["rss_off"])
     graphs = {}
     if "uneven" in parts and not args.no_graph:
         graphs["uneven"] = capture_uneven(sn, work)
@@ -329,6 +337,7 @@ def bench_ours(args, rank, world, local_rank, dist):
         "wall_s_timed_loop": round(wall, 3),
     }
 
+    result["config"]["launch_parameters"] = tuned or "library defaults"
     result["config"]["uneven_launch"] = ("replay of a captured CUDA graph (plan memset, plan / bin / tile / RSS "
                                          "kernels, scratch allocation nodes)" if graphs else "direct call")
     if not args.no_e2e:
@@ -341,6 +350,12 @@ def bench_ours(args, rank, world, local_rank, dist):
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(sizes, budget_s=12.0)
     return result
+
+
+def autotune(sn, keys, vals, offsets):
+    """sn_tune_segments on a batch; returns the installed parameters and the tuned time."""
+    params, ms = sn.sn_tune_segments(keys, vals, offsets)
+    return dict(params, tuned_ms=round(ms, 4))
 
 
 def capture_uneven(sn, w):
@@ -397,6 +412,11 @@ def bench_plain_vs_batched(args, sn, device, dist):
         def batched():
             sn.check(seg(work_b, None, d_off), "batched")
 
+        tuning = "library defaults"
+        if not args.no_tune:
+            work_b.copy_(keys)
+            tuning = autotune(sn, work_b, None, d_off)
+
         res = {}
         for label, fn, src, dst in (("plain", plain, grouped, work_p), ("batched", batched, keys, work_b)):
             for _ in range(max(3, args.warmup)):
@@ -423,7 +443,8 @@ def bench_plain_vs_batched(args, sn, device, dist):
         out[name] = {"plain_ms": round(ms_p, 4), "plain_gkeys_s": round(total / (ms_p * 1e-3) / 1e9, 2),
                      "plain_launches": int(sum(1 for n in range(2, 17) if counts[n])),
                      "batched_ms": round(ms_b, 4), "batched_gkeys_s": round(total / (ms_b * 1e-3) / 1e9, 2),
-                     "batched_launches": 4, "batched_over_plain": round(ms_p / ms_b, 3)}
+                     "batched_launches": 4, "batched_over_plain": round(ms_p / ms_b, 3),
+                     "batched_launch_parameters": tuning}
         del keys, grouped, work_b, work_p, views
     return out
 
@@ -453,6 +474,13 @@ def bench_serving(args, device):
     max_cnt = min(100_000, pool_nseg)
     counts = np.floor(np.exp(rng.uniform(0.0, np.log(max_cnt + 1), n_req))).astype(np.int64).clip(1, max_cnt)
     starts = rng.integers(0, pool_nseg - counts + 1)
+    tuning = "library defaults"
+    if not args.no_tune:  # tune on the first 10^6 pool segments (same length mix)
+        import paper_2002_05599_gb300 as sn
+        m = min(pool_nseg, 1_000_000)
+        dk = keys_in[:int(off[m])].to(device)
+        tuning = autotune(sn, dk, None, torch.from_numpy(off[:m + 1].view(np.int32)).to(device))
+        del dk
     budget = 40 << 30
     srv = SortServer(budget_bytes=budget, key_bytes=4, slots=4)
     lib, h = _lib(), srv._h
@@ -483,6 +511,7 @@ def bench_serving(args, device):
     return {"requests": n_req, "rate_hz": args.serve_rate, "seconds": round(span, 3),
             "segments_per_request": "log-uniform 1..1e5", "segment_lengths": "uniform 2..256",
             "keys": "u32 uniform, pinned host memory", "budget_gb": budget / 2**30, "slots": 4,
+            "launch_parameters": tuning,
             "offered_gkeys_s": round(keys_req / span / 1e9, 2),
             "achieved_gkeys_s": round(st["keys_per_s"] / 1e9, 2),
             "p50_ms": round(st["latency_p50_us"] / 1e3, 3), "p99_ms": round(st["latency_p99_us"] / 1e3, 3),

@@ -134,23 +134,26 @@ int sn_sort_segments_u64_noalloc(uint64_t *keys, uint32_t *vals, const uint32_t 
  * results.
  */
 typedef struct {
-    int tile_units;        /* segments + items per tile of the network kernel: 512..8192 (default 2048);
-                              at most 4096 unless keys are u32 without payload (shared memory) */
+    int tile_units;        /* segments + items per tile of the network kernel: 512..8192 (default 2048) */
     unsigned net_classes;  /* padded network sizes for 2..16-item segments: bit 0 = 2, bit 1 = 4,
                               bit 2 = 8, bit 3 = 12 channels; 16 channels always (default 0xF) */
     int rss_two_min;       /* Register Sample Sort: segments longer than this draw a 64-item sample,
                               shorter ones 32 (16..256, default 160) */
+    int tile_stages;       /* staging depth of the network kernel: 2..4 tiles in flight per block
+                              (default 2); tile_stages x tile size must fit in shared memory */
 } sn_tuning;
 
 /* Current parameters of the current device for (key_bytes = 4 or 8, with_vals = 0 or 1). */
 int sn_tuning_get(int key_bytes, int with_vals, sn_tuning *out);
-/* Installs parameters (SN_EINVAL if out of range). */
+/* Installs parameters (SN_EINVAL if out of range, or if tile_stages tiles of
+   tile_units do not fit in shared memory for this key type and payload kind:
+   two 8192-unit stages fit only for u32 keys without payload). */
 int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning *t);
 /*
  * Autotuner: times sn_sort_segments on the caller's batch (device pointers,
  * same contract as sn_sort_segments / _u64 with key_bytes 4 / 8) under
- * candidate parameters -- a coordinate search over net_classes, tile_units
- * and rss_two_min, best of three runs each, the input restored from a device
+ * candidate parameters -- a coordinate search over net_classes, (tile_units,
+ * tile_stages) and rss_two_min, best of three runs each, the input restored from a device
  * copy before every run -- installs the fastest set for this key type and
  * payload kind on the current device and copies it to `out` (may be NULL).
  * Synchronous: returns after the search; the batch is left sorted.

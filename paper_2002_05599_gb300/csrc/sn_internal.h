@@ -29,6 +29,7 @@ struct SegTuning {
   int tile_units = 2048;       // segments + elements per tile (512..8192)
   uint32_t net_classes = 0xF;  // padded network classes in use: bit q = 2, 4, 8, 12 channels (16 always)
   int rss_two_min = 160;       // RSS segments longer than this take a 64-item sample, else 32 (16..256)
+  int tile_stages = 2;         // staging depth of the tile kernel (2..4)
 };
 
 // Parameters installed for (device, key bytes, payload) (sn_tune.cu); the
@@ -36,11 +37,12 @@ struct SegTuning {
 SegTuning current_tuning(int device, int key_bytes, bool vals);
 bool tuning_valid(const SegTuning& t);
 
-// Largest tile_units whose staging fits in shared memory (sn_segments_*.cu).
-int max_tile_units_u32(bool vals);
-int max_tile_units_u64(bool vals);
-inline int max_tile_units(int key_bytes, bool vals) {
-  return key_bytes == 8 ? max_tile_units_u64(vals) : max_tile_units_u32(vals);
+// Whether the tile kernel's staging (tile_units, tile_stages) fits in shared
+// memory for this key type and payload kind (sn_segments_*.cu).
+bool tile_fits_u32(bool vals, int tile_units, int stages);
+bool tile_fits_u64(bool vals, int tile_units, int stages);
+inline bool tile_fits(int key_bytes, bool vals, int tile_units, int stages) {
+  return key_bytes == 8 ? tile_fits_u64(vals, tile_units, stages) : tile_fits_u32(vals, tile_units, stages);
 }
 
 // Device scratch needed for a segmented call with nseg segments.

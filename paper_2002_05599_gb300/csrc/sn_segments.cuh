@@ -53,7 +53,7 @@ namespace {  // internal linkage: each instantiation unit gets its own copy
 constexpr int kTileWarps = 8;
 constexpr int kTileConsumers = kTileWarps * 32;
 constexpr int kTileThreads = kTileConsumers + 32;  // + one producer warp
-constexpr int kStages = 2;
+constexpr int kMaxStages = 4;  // tile-kernel staging depth: 2..4 stages (a launch parameter)
 constexpr int kRssWarps = 8;
 constexpr int kRssThreads = kRssWarps * 32;
 constexpr int kMaxSeg = 256;
@@ -97,7 +97,8 @@ __host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~stati
 
 template <class K, bool kVals>
 struct TileLayout {
-  size_t off_at, key_at, val_at, ord_at, cnt_at, stage_bytes, total;
+  size_t off_at, key_at, val_at, ord_at, cnt_at, stage_bytes;
+  __host__ __device__ size_t total(int stages) const { return stages * stage_bytes; }
   __host__ __device__ explicit TileLayout(uint32_t E) {
     off_at = 0;
     key_at = align16(off_at + (E + 1 + 8) * 4);
@@ -105,7 +106,6 @@ struct TileLayout {
     ord_at = align16(val_at + (kVals ? (E + kMaxSeg + 8) * 4 : 0));
     cnt_at = align16(ord_at + (E + 16) * 2);
     stage_bytes = align128(cnt_at + 16);
-    total = kStages * stage_bytes;
   }
 };
 
@@ -645,7 +645,7 @@ __device__ __forceinline__ TileTasks tile_tasks(const uint16_t* cnt) {
   return t;
 }
 
-template <class K, bool kVals>
+template <class K, bool kVals, int kStages>
 __global__ void __launch_bounds__(kTileThreads, 2)
     seg_tile_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
                     const Plan* plan, const uint32_t* __restrict__ tile_first, const uint16_t* __restrict__ counts,
@@ -718,7 +718,8 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       // stage the next tile when its stage is free (lane 0 tests, all lanes follow)
       bool can_issue = false;
       if (lane == 0)
-        can_issue = avail != 0 && (issued < kStages || mbar_test(&empty[issued & 1], ((issued >> 1) - 1) & 1u));
+        can_issue = avail != 0 && (issued < kStages || mbar_test(&empty[issued % kStages],
+                                                                   ((issued / kStages) - 1) & 1u));
       can_issue = __shfl_sync(kFull, can_issue, 0);
       if (can_issue) {
         const int j = __ffs(avail) - 1;
@@ -728,7 +729,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                        e1j = __shfl_sync(kFull, e1, j);
         bool staged = true;
         if (lane == 0) {
-          const int s = issued & 1;
+          const int s = static_cast<int>(issued % kStages);
           unsigned char* stage = smem + s * lay.stage_bytes;
           // granule-rounded source ranges (a 16-byte granule never crosses a
           // page, so reading its unused part cannot fault; it is discarded)
@@ -788,10 +789,10 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       }
       // publish the work items of the oldest staged tile once it has landed
       bool can_push = false;
-      if (lane == 0) can_push = pushed < issued && mbar_test(&full[pushed & 1], (pushed >> 1) & 1u);
+      if (lane == 0) can_push = pushed < issued && mbar_test(&full[pushed % kStages], (pushed / kStages) & 1u);
       can_push = __shfl_sync(kFull, can_push, 0);
       if (can_push) {
-        const int s = pushed & 1;
+        const int s = static_cast<int>(pushed % kStages);
         // only lane 0 observed the copy's completion, so only lane 0 reads the
         // staged counts; the task count is broadcast
         uint32_t ntasks = 0;
@@ -800,7 +801,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         ntasks = __shfl_sync(kFull, ntasks, 0);
         const TileTasks tt{0, 0, ntasks, 0, 0, 0, 0, 0};
         // item = stage << 17 | phase parity of this use of the stage << 16 | index
-        const uint32_t tag = (static_cast<uint32_t>(s) << 17) | (((pushed >> 1) & 1u) << 16);
+        const uint32_t tag = (static_cast<uint32_t>(s) << 17) | (((pushed / kStages) & 1u) << 16);
         for (uint32_t i = lane; i < tt.ntasks; i += 32) ring[(tail + i) & (kRing - 1)] = tag | i;
         if (lane == 0) ntasks_of[s] = tt.ntasks;
         __syncwarp();
@@ -1087,28 +1088,28 @@ __global__ void __launch_bounds__(kRssThreads, 2)
 constexpr int kCacheDevices = 64;
 constexpr int kCacheTileSizes = 5;  // tile_units 512, 1024, ..., 8192 (powers of two); others are not cached
 
-// Cache entry of a launch shape for device d and tile size E (null: do not cache).
-inline std::atomic<int>* cache_slot(std::atomic<int>* cache, const DeviceInfo& d, uint32_t E) {
+// Cache entry of a launch shape for device d, tile size E and staging depth
+// (null: do not cache).
+inline std::atomic<int>* cache_slot(std::atomic<int>* cache, const DeviceInfo& d, uint32_t E, int stages) {
   int t = 0;
   if (E) {
     if (E & (E - 1)) return nullptr;
     t = 31 - __builtin_clz(E) - 9;
     if (t < 0 || t >= kCacheTileSizes) return nullptr;
   }
-  if (d.device < 0 || d.device >= kCacheDevices) return nullptr;
-  return &cache[d.device * kCacheTileSizes + t];
+  if (d.device < 0 || d.device >= kCacheDevices || stages < 1 || stages > kMaxStages) return nullptr;
+  return &cache[(d.device * kCacheTileSizes + t) * kMaxStages + (stages - 1)];
 }
 
 // Dynamic shared memory a tile-kernel block may take (the 227 KB per-block
 // limit less a margin for the kernel's static shared memory).
 constexpr size_t kTileSmemLimit = 232448 - 4096;
 
-// Largest power-of-two tile size (512..8192) whose two stages fit.
+// Whether `stages` stages of E-unit tiles fit in a block's shared memory.
 template <class K, bool kVals>
-int max_tile_units_for() {
-  for (uint32_t E = 8192; E >= 512; E >>= 1)
-    if (TileLayout<K, kVals>(E).total <= kTileSmemLimit) return static_cast<int>(E);
-  return 0;
+bool tile_fits(int E, int stages) {
+  return E >= 512 && E <= 8192 && stages >= 2 && stages <= kMaxStages &&
+         TileLayout<K, kVals>(static_cast<uint32_t>(E)).total(stages) <= kTileSmemLimit;
 }
 
 // Resident blocks per SM of `kern` with `smem` bytes of dynamic shared
@@ -1155,12 +1156,14 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
 
   {
     const TileLayout<K, kVals> lay(E);
-    const int smem_bytes = static_cast<int>(lay.total);
-    auto kern = seg_tile_kernel<K, kVals>;
-    static std::atomic<int> cache[kCacheDevices * kCacheTileSizes];
+    const int smem_bytes = static_cast<int>(lay.total(tun.tile_stages));
+    auto kern = tun.tile_stages == 2   ? seg_tile_kernel<K, kVals, 2>
+                : tun.tile_stages == 3 ? seg_tile_kernel<K, kVals, 3>
+                                       : seg_tile_kernel<K, kVals, 4>;
+    static std::atomic<int> cache[kCacheDevices * kCacheTileSizes * kMaxStages];
     int per_sm = 0;
-    const int attr = static_cast<int>(TileLayout<K, kVals>(max_tile_units_for<K, kVals>()).total);
-    if ((e = blocks_per_sm(kern, kTileThreads, smem_bytes, attr, cache_slot(cache, d, E), &per_sm)) != cudaSuccess)
+    if ((e = blocks_per_sm(kern, kTileThreads, smem_bytes, static_cast<int>(kTileSmemLimit),
+                           cache_slot(cache, d, E, tun.tile_stages), &per_sm)) != cudaSuccess)
       return e;
     const unsigned g3 = static_cast<unsigned>(
         std::max<uint64_t>(1, std::min<uint64_t>(sl.cap - 1, static_cast<uint64_t>(d.sm_count) * per_sm)));
@@ -1172,9 +1175,9 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
     using WL = RssWarpLayout<K, kVals>;
     const int smem_bytes = static_cast<int>(kRssWarps * WL::kBytes);
     auto kern = seg_rss_kernel<K, kVals>;
-    static std::atomic<int> cache[kCacheDevices * kCacheTileSizes];
+    static std::atomic<int> cache[kCacheDevices * kCacheTileSizes * kMaxStages];
     int per_sm = 0;
-    if ((e = blocks_per_sm(kern, kRssThreads, smem_bytes, smem_bytes, cache_slot(cache, d, 0), &per_sm)) !=
+    if ((e = blocks_per_sm(kern, kRssThreads, smem_bytes, smem_bytes, cache_slot(cache, d, 0, 2), &per_sm)) !=
         cudaSuccess)
       return e;
     const uint64_t tiles_cap = sl.cap - 1;
@@ -1193,7 +1196,7 @@ cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, ui
                             const DeviceInfo& d) {
   if (t.tile_units < 512 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg || t.net_classes > 0xFu)
     return cudaErrorInvalidValue;
-  if (t.tile_units > (vals ? max_tile_units_for<K, true>() : max_tile_units_for<K, false>()))
+  if (!(vals ? tile_fits<K, true>(t.tile_units, t.tile_stages) : tile_fits<K, false>(t.tile_units, t.tile_stages)))
     return cudaErrorInvalidValue;
   if (scratch_bytes < ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total) return cudaErrorInvalidValue;
   const bool rss = mode == SegMode::kRssOnly;

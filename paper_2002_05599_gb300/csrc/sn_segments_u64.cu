@@ -9,8 +9,8 @@ cudaError_t launch_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* 
   return seg::launch_segments<uint64_t>(keys, vals, offsets, nseg, mode, scratch, scratch_bytes, t, s, d);
 }
 
-int max_tile_units_u64(bool vals) {
-  return vals ? seg::max_tile_units_for<uint64_t, true>() : seg::max_tile_units_for<uint64_t, false>();
+bool tile_fits_u64(bool vals, int tile_units, int stages) {
+  return vals ? seg::tile_fits<uint64_t, true>(tile_units, stages) : seg::tile_fits<uint64_t, false>(tile_units, stages);
 }
 
 }  // namespace sn

@@ -3,8 +3,9 @@
 //
 // The table holds one SegTuning per (device, key type, payload kind).  The
 // tuner is a coordinate search: starting from the installed set it sweeps one
-// parameter at a time over its candidates with the others fixed, keeps a
-// candidate only if it is more than 1% faster, and makes two passes.  Every
+// parameter at a time over its candidates with the others fixed (skipping
+// tile shapes whose staging does not fit in shared memory), keeps a candidate
+// only if it is more than 1% faster, and makes two passes.  Every
 // timing restores the caller's batch from a device copy, then times one
 // sn_sort_segments launch sequence with CUDA events on the caller's stream;
 // the best of three runs counts.
@@ -28,7 +29,7 @@ bool g_touched[kDevs][2][2];
 
 bool tuning_valid(const SegTuning& t) {
   return t.tile_units >= 512 && t.tile_units <= 8192 && t.net_classes <= 0xFu && t.rss_two_min >= 16 &&
-         t.rss_two_min <= SN_MAX_SEGMENT;
+         t.rss_two_min <= SN_MAX_SEGMENT && t.tile_stages >= 2 && t.tile_stages <= 4;
 }
 
 SegTuning current_tuning(int device, int key_bytes, bool vals) {
@@ -50,6 +51,7 @@ sn_tuning to_c(const SegTuning& t) {
   c.tile_units = t.tile_units;
   c.net_classes = t.net_classes;
   c.rss_two_min = t.rss_two_min;
+  c.tile_stages = t.tile_stages;
   return c;
 }
 
@@ -58,6 +60,7 @@ SegTuning from_c(const sn_tuning& c) {
   t.tile_units = c.tile_units;
   t.net_classes = c.net_classes;
   t.rss_two_min = c.rss_two_min;
+  t.tile_stages = c.tile_stages;
   return t;
 }
 
@@ -97,7 +100,8 @@ int sn_tuning_get(int key_bytes, int with_vals, sn_tuning* out) {
 int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning* t) {
   if (t == nullptr || (key_bytes != 4 && key_bytes != 8)) return SN_EINVAL;
   const sn::SegTuning st = sn::from_c(*t);
-  if (!sn::tuning_valid(st) || st.tile_units > sn::max_tile_units(key_bytes, with_vals != 0)) return SN_EINVAL;
+  if (!sn::tuning_valid(st) || !sn::tile_fits(key_bytes, with_vals != 0, st.tile_units, st.tile_stages))
+    return SN_EINVAL;
   int err = SN_OK;
   const sn::DeviceInfo* d = sn::device_info(&err);
   if (d == nullptr) return err;
@@ -178,6 +182,7 @@ int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64
   sn::SegTuning best = sn::current_tuning(d->device, key_bytes, with_vals);
   float best_t = time_of(best);
   static const int kTiles[] = {512, 1024, 2048, 4096, 8192};
+  static const int kStagesC[] = {2, 3, 4};
   static const int kTwo[] = {32, 64, 96, 128, 160, 192, 224, 256};
   for (int pass = 0; pass < 2 && !failed; ++pass) {
     for (unsigned mask = 0; mask <= 0xFu && !failed; ++mask) {
@@ -188,11 +193,16 @@ int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64
       if (t < 0.99f * best_t) best = c, best_t = t;
     }
     for (int tu : kTiles) {
-      if (failed || tu == best.tile_units || tu > sn::max_tile_units(key_bytes, with_vals)) continue;
-      sn::SegTuning c = best;
-      c.tile_units = tu;
-      const float t = time_of(c);
-      if (t < 0.99f * best_t) best = c, best_t = t;
+      for (int st : kStagesC) {
+        if (failed || (tu == best.tile_units && st == best.tile_stages) ||
+            !sn::tile_fits(key_bytes, with_vals, tu, st))
+          continue;
+        sn::SegTuning c = best;
+        c.tile_units = tu;
+        c.tile_stages = st;
+        const float t = time_of(c);
+        if (t < 0.99f * best_t) best = c, best_t = t;
+      }
     }
     for (int two : kTwo) {
       if (failed || two == best.rss_two_min) continue;
@@ -219,7 +229,7 @@ int sn_tuning_save(const char* path) {
   if (path == nullptr) return SN_EINVAL;
   FILE* f = std::fopen(path, "w");
   if (f == nullptr) return SN_EINVAL;
-  bool ok = std::fprintf(f, "smallsort-tuning 1\n") > 0;
+  bool ok = std::fprintf(f, "smallsort-tuning 2\n") > 0;
   {
     std::lock_guard<std::mutex> lk(sn::g_mu);
     for (int dev = 0; dev < sn::kDevs; ++dev)
@@ -227,8 +237,8 @@ int sn_tuning_save(const char* path) {
         for (int v = 0; v < 2; ++v)
           if (sn::g_touched[dev][u64][v]) {
             const sn::SegTuning& t = sn::g_table[dev][u64][v];
-            ok = ok && std::fprintf(f, "%d %d %d %d %u %d\n", dev, u64 ? 8 : 4, v, t.tile_units, t.net_classes,
-                                    t.rss_two_min) > 0;
+            ok = ok && std::fprintf(f, "%d %d %d %d %u %d %d\n", dev, u64 ? 8 : 4, v, t.tile_units,
+                                    t.net_classes, t.rss_two_min, t.tile_stages) > 0;
           }
   }
   ok = (std::fclose(f) == 0) && ok;
@@ -240,7 +250,7 @@ int sn_tuning_load(const char* path) {
   FILE* f = std::fopen(path, "r");
   if (f == nullptr) return SN_EINVAL;
   int version = 0;
-  if (std::fscanf(f, "smallsort-tuning %d\n", &version) != 1 || version != 1) {
+  if (std::fscanf(f, "smallsort-tuning %d\n", &version) != 1 || version != 2) {
     std::fclose(f);
     return SN_EINVAL;
   }
@@ -249,16 +259,17 @@ int sn_tuning_load(const char* path) {
     cudaGetLastError();
     ndev = 0;
   }
-  int dev, kb, v, tu, two;
+  int dev, kb, v, tu, two, st;
   unsigned mask;
   int rc = SN_OK, n;
-  while ((n = std::fscanf(f, "%d %d %d %d %u %d", &dev, &kb, &v, &tu, &mask, &two)) == 6) {
+  while ((n = std::fscanf(f, "%d %d %d %d %u %d %d", &dev, &kb, &v, &tu, &mask, &two, &st)) == 7) {
     sn::SegTuning t;
     t.tile_units = tu;
     t.net_classes = mask;
     t.rss_two_min = two;
+    t.tile_stages = st;
     if (dev < 0 || dev >= sn::kDevs || (kb != 4 && kb != 8) || (v != 0 && v != 1) || !sn::tuning_valid(t) ||
-        t.tile_units > sn::max_tile_units(kb, v != 0)) {
+        !sn::tile_fits(kb, v != 0, t.tile_units, t.tile_stages)) {
       rc = SN_EINVAL;
       break;
     }

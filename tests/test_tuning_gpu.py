@@ -11,10 +11,11 @@ from gpu_util import to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-SETS = [dict(tile_units=512, net_classes=0x0, rss_two_min=16),
-        dict(tile_units=4096, net_classes=0xF, rss_two_min=256),
-        dict(tile_units=1024, net_classes=0x5, rss_two_min=64),
-        dict(tile_units=4096, net_classes=0xA, rss_two_min=200)]
+SETS = [dict(tile_units=512, net_classes=0x0, rss_two_min=16, tile_stages=2),
+        dict(tile_units=4096, net_classes=0xF, rss_two_min=256, tile_stages=2),
+        dict(tile_units=1024, net_classes=0x5, rss_two_min=64, tile_stages=4),
+        dict(tile_units=2048, net_classes=0xA, rss_two_min=200, tile_stages=3),
+        dict(tile_units=512, net_classes=0x4, rss_two_min=128, tile_stages=3)]
 
 
 @pytest.fixture
@@ -52,6 +53,8 @@ def test_tile_size_limit_by_shared_memory(restore_defaults):
     for kb, v in ((4, True), (8, False), (8, True)):
         assert sn.sn_tuning_set(kb, v, tile_units=8192) == sn.SN_EINVAL
         assert sn.sn_tuning_set(kb, v, tile_units=4096) == sn.SN_OK
+        assert sn.sn_tuning_set(kb, v, tile_units=4096, tile_stages=4) == sn.SN_EINVAL
+        assert sn.sn_tuning_set(kb, v, tile_units=2048, tile_stages=4) == sn.SN_OK
     k, _, off = wl.segment_batch(50_000, "geometric", "uniform", np.uint32, False, seed=79, p=0.15, cap=256)
     dk = to_dev(k)
     sn.check(sn.sn_tuning_set(4, False, tile_units=8192), "set")
