@@ -290,8 +290,7 @@ __device__ __forceinline__ uint64_t hi_of(uint64_t a, uint64_t b) { return max(a
 // even lane and the 16 largest on the odd lane, each a bitonic sequence that
 // four in-register half-cleaner levels sort.
 template <class T>
-__device__ __forceinline__ void pair_network32(T (&x)[16], bool upper) {
-  Net<16>::run(x);
+__device__ __forceinline__ void pair_merge(T (&x)[16], bool upper) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const T a = shfl_xor(x[15 - q], 1);
@@ -312,12 +311,17 @@ __device__ __forceinline__ void pair_network32(T (&x)[16], bool upper) {
   }
 }
 
-// Segment of 17..32 items handled by lanes (lane & ~1, lane | 1).  Lanes whose
-// pair has no segment (active = false) still take part in the shuffles.
+// The 16-channel path shared by two kinds of work item, so that the GPU runs
+// one copy of the 16-channel network code for both:
+//  * pair = false: the lane's own segment of L <= 16 items (padded to 16);
+//  * pair = true:  a segment of 17..32 items on lanes (lane & ~1, lane | 1):
+//    the even lane holds items 0..15, the odd lane 16..31; after the network
+//    the lanes merge (pair_merge).  `pair` is warp-uniform.
+// Lanes without a segment (active = false) still take part in the shuffles.
 template <class K, bool kVals>
-__device__ __forceinline__ void pair_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, bool active,
-                                             int lane) {
-  const bool upper = lane & 1;
+__device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, int L, bool active, bool pair,
+                                      int lane) {
+  const bool upper = pair && (lane & 1);
   const int base = upper ? 16 : 0;
   if constexpr (kVals) {
     using IO = ItemOf<K>;
@@ -325,7 +329,8 @@ __device__ __forceinline__ void pair_segment(K* kbuf, uint32_t* vbuf, int p, int
 #pragma unroll
     for (int q = 0; q < 16; ++q)
       x[q] = (active && base + q < L) ? IO::make(kbuf[p + base + q], base + q) : IO::sentinel(base + q);
-    pair_network32(x, upper);
+    Net<16>::run(x);
+    if (pair) pair_merge(x, upper);
     uint32_t v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q)
@@ -343,7 +348,8 @@ __device__ __forceinline__ void pair_segment(K* kbuf, uint32_t* vbuf, int p, int
 #pragma unroll
     for (int q = 0; q < 16; ++q)
       x[q] = (active && base + q < L) ? kbuf[p + base + q] : static_cast<K>(~static_cast<K>(0));
-    pair_network32(x, upper);
+    Net<16>::run(x);
+    if (pair) pair_merge(x, upper);
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < 16; ++q)
@@ -891,13 +897,24 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       L = o1 - o;
       return o1 - e0 + key_shift <= key_cap && o1 - e0 + val_shift <= val_cap;
     };
-    if (task < tt.pair_tasks) {
-      const uint32_t slot = task * 16 + (lane >> 1);
-      bool active = slot < tt.npair;
-      int p = 0, pv = 0, L = 0;
+    // every work item: the lane's segment, its class and its staged position
+    const bool pair = task < tt.pair_tasks;
+    bool active = false;
+    int p = 0, pv = 0, L = 0, cls = 16;
+    {
+      uint32_t slot, first = 0;
+      if (pair) {
+        slot = task * 16 + (lane >> 1);
+        active = slot < tt.npair;
+      } else {
+        first = tt.npair + (task - tt.pair_tasks) * 32;
+        slot = first + lane;
+        active = slot < tt.b2;
+        cls = first < tt.b16 ? 16 : first < tt.b12 ? 12 : first < tt.b8 ? 8 : first < tt.b4 ? 4 : 2;
+      }
       if (active) {
         uint32_t o = 0, l = 0;
-        if (span_ok(ord[slot], o, l)) {
+        if (span_ok(ord[slot], o, l) && (pair || l <= 16)) {
           L = static_cast<int>(l);
           p = static_cast<int>(o - e0 + key_shift);
           pv = static_cast<int>(o - e0 + val_shift);
@@ -906,28 +923,18 @@ __global__ void __launch_bounds__(kTileThreads, 2)
           active = false;
         }
       }
-      pair_segment<K, kVals>(kbuf, vbuf, p, pv, L, active, lane);
-    } else {
-      const uint32_t first = tt.npair + (task - tt.pair_tasks) * 32;
-      const uint32_t slot = first + lane;
-      uint32_t o = 0, l = 0;
-      const bool ok_seg = slot < tt.b2 && span_ok(ord[slot], o, l) && l <= 16;
-      if (slot < tt.b2 && !ok_seg) atomicOr(status, kStatusInternal | kCheckSegment);
-      if (ok_seg) {
-        const int L = static_cast<int>(l);
-        const int p = static_cast<int>(o - e0 + key_shift);
-        const int pv = static_cast<int>(o - e0 + val_shift);
-        if (first < tt.b16)
-          net_segment<16, K, kVals>(kbuf, vbuf, p, pv, L);
-        else if (first < tt.b12)
-          net_segment<12, K, kVals>(kbuf, vbuf, p, pv, L);
-        else if (first < tt.b8)
-          net_segment<8, K, kVals>(kbuf, vbuf, p, pv, L);
-        else if (first < tt.b4)
-          net_segment<4, K, kVals>(kbuf, vbuf, p, pv, L);
-        else
-          net_segment<2, K, kVals>(kbuf, vbuf, p, pv, L);
-      }
+    }
+    if (cls == 16) {
+      seg16<K, kVals>(kbuf, vbuf, p, pv, L, active, pair, lane);
+    } else if (active) {
+      if (cls == 12)
+        net_segment<12, K, kVals>(kbuf, vbuf, p, pv, L);
+      else if (cls == 8)
+        net_segment<8, K, kVals>(kbuf, vbuf, p, pv, L);
+      else if (cls == 4)
+        net_segment<4, K, kVals>(kbuf, vbuf, p, pv, L);
+      else
+        net_segment<2, K, kVals>(kbuf, vbuf, p, pv, L);
     }
 
     // completion: the warp that finishes a tile's last item stores the tile
