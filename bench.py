@@ -210,14 +210,17 @@ def launches_per_step(parts=("sweep", "uneven", "rss")):
 PARTS = ("sweep", "uneven", "rss")
 
 
-def run_parts(sn, w, events=None, parts=PARTS, graphs=None):
-    """One step on the current stream; events[0..3] bracket sweep / uneven / rss.
+def run_parts(sn, w, events=None, parts=PARTS, graphs=None, n_events=None):
+    """One step on the current stream; events[0..3] bracket sweep / uneven / rss,
+    n_events[i] (optional) follows the sort of the i-th fixed n.
     graphs["uneven"], when given, is the captured uneven-batch call."""
     if events:
         events[0].record()
     if "sweep" in parts:
-        for n in SWEEP_NS:
+        for i, n in enumerate(SWEEP_NS):
             sn.check(sn.sn_sort_fixed(w[f"sweep{n}"], n), f"sn_sort_fixed n={n}")
+            if n_events:
+                n_events[i].record()
     if events:
         events[1].record()
     if "uneven" in parts:
@@ -273,6 +276,7 @@ def bench_ours(args, rank, world, local_rank, dist):
         sn.check(sn.sn_check(), "graph warm-up")
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    nev = [[torch.cuda.Event(enable_timing=True) for _ in SWEEP_NS] for _ in range(args.steps)]
     sampler = ClockSampler(local_rank) if rank == 0 else None
     if dist:
         dist.barrier()
@@ -283,7 +287,7 @@ def bench_ours(args, rank, world, local_rank, dist):
     t0 = time.perf_counter()
     for k in range(args.steps):
         restore()
-        run_parts(sn, work, ev[k], parts=parts, graphs=graphs)
+        run_parts(sn, work, ev[k], parts=parts, graphs=graphs, n_events=nev[k])
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clocks = sampler.stop() if sampler else None
@@ -308,6 +312,15 @@ def bench_ours(args, rank, world, local_rank, dist):
     hbm, hbm_src = peaks()
     sweep_gbs = bytes_["sweep"] / (ms["sweep"] * 1e-3) / 1e9 if "sweep" in parts else 0.0
     parts_out = {}
+    if "sweep" in parts:  # per n: time between the events around its launch, mean over steps
+        per_n = {}
+        for i, n in enumerate(SWEEP_NS):
+            t = statistics.mean((e[0] if i == 0 else ne[i - 1]).elapsed_time(ne[i]) for e, ne in zip(ev, nev))
+            b = 8 * pristine[f"sweep{n}"].numel()
+            per_n[n] = {"ms": round(t, 4), "gkeys_s": round(b / 8 / (t * 1e-3) / 1e9, 1),
+                        "frac_hbm": round(b / (t * 1e-3) / 1e9 / hbm, 4)}
+        parts_out["sweep_per_n"] = per_n
+        parts_out["sweep_min_frac_hbm"] = min(v["frac_hbm"] for v in per_n.values())
     for p in parts:
         gbs = bytes_[p] / (ms[p] * 1e-3) / 1e9
         parts_out[p] = {"ms": round(ms[p], 4), "gkeys_s": round(keys[p] / (ms[p] * 1e-3) / 1e9, 2),

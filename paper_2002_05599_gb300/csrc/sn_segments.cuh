@@ -516,12 +516,35 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
     const int e = (r << 5) + lane;
     x[r] = (r < rounds && e < L) ? IO::make(kbuf[p + e], e) : IO::sentinel(0);
   }
+  // The top levels have few distinct nodes: they are broadcast once per
+  // segment and picked with selects (nodes 1..7 for 8-byte items, 1..3 for
+  // the 12-byte items of u64 keys); the deeper levels read node j of lane j.
+  constexpr bool kNarrow = sizeof(It) == 8;
+  const It n1 = shfl_idx(tree, 1), n2 = shfl_idx(tree, 2), n3 = shfl_idx(tree, 3);
+  It n4 = n1, n5 = n1, n6 = n1, n7 = n1;
+  if constexpr (kNarrow) {
+    n4 = shfl_idx(tree, 4);
+    n5 = shfl_idx(tree, 5);
+    n6 = shfl_idx(tree, 6);
+    n7 = shfl_idx(tree, 7);
+  }
 #pragma unroll
-  for (int lv = 0; lv < 5; ++lv) {
+  for (int r = 0; r < 8; ++r) {
+    if (r < rounds) {
+      j[r] = 2 + (item_less(n1, x[r]) ? 1 : 0);
+      j[r] = 2 * j[r] + (item_less(j[r] & 1 ? n3 : n2, x[r]) ? 1 : 0);
+    }
+  }
+#pragma unroll
+  for (int lv = 2; lv < 5; ++lv) {
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       if (r < rounds) {
-        const It t = shfl_idx(tree, j[r]);
+        It t;
+        if (kNarrow && lv == 2)
+          t = j[r] & 2 ? (j[r] & 1 ? n7 : n6) : (j[r] & 1 ? n5 : n4);
+        else
+          t = shfl_idx(tree, j[r]);
         j[r] = 2 * j[r] + (item_less(t, x[r]) ? 1 : 0);
       }
     }
@@ -1027,7 +1050,9 @@ __global__ void __launch_bounds__(kRssThreads, 2)
 
   auto sort_staged = [&](uint32_t d) {  // sort segment number d of this warp
     const int b = d & 1;
-    if (!mbar_wait(&bar[b], (d >> 1) & 1u)) {
+    // every lane waits itself (bulk-copy data is visible to the lanes that
+    // observe the phase); a timeout anywhere fails the whole warp
+    if (!__all_sync(kFull, mbar_wait(&bar[b], (d >> 1) & 1u))) {
       if (lane == 0) atomicOr(status, kStatusTimeout);
       failed = true;
       return;
@@ -1060,29 +1085,29 @@ __global__ void __launch_bounds__(kRssThreads, 2)
         s0 = tile_first[t];
       }
     }
-    unsigned mask = __ballot_sync(kFull, rc != 0);
-    while (mask && !failed) {
-      const int j = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const uint32_t rcj = __shfl_sync(kFull, rc, j), s0j = __shfl_sync(kFull, s0, j),
-                     basej = __shfl_sync(kFull, base, j);
-      for (uint32_t q0 = 0; q0 < rcj && !failed; q0 += 32) {
-        uint32_t e0q = 0, Lq = 0;
-        if (q0 + lane < rcj) {
-          const uint32_t local = order[s0j + basej + q0 + lane];
-          e0q = offsets[s0j + local];
-          Lq = offsets[s0j + local + 1] - e0q;
-        }
-        const uint32_t n = min(32u, rcj - q0);
-        for (uint32_t r = 0; r < n && !failed; ++r) {
-          const uint32_t ne0 = __shfl_sync(kFull, e0q, r), nL = __shfl_sync(kFull, Lq, r);
-          // stage segment number `issued`, then sort the previous one while it loads
-          if (lane == 0) rss_issue<K, kVals>(wbase, issued & 1, &bar[issued & 1], keys, vals, ne0, nL);
-          ++issued;
-          if (issued >= 2) sort_staged(issued - 2);
-          pe0 = ne0;
-          pL = nL;
-        }
+    // round j: lane i fetches the j-th RSS segment of its tile (one round
+    // trip per round for all 32 tiles of the chunk); the segments found are
+    // staged and sorted in lane order
+    const uint32_t rounds = __reduce_max_sync(kFull, rc);
+    for (uint32_t j = 0; j < rounds && !failed; ++j) {
+      uint32_t e0q = 0, Lq = 0;
+      const bool has = j < rc;
+      if (has) {
+        const uint32_t local = order[s0 + base + j];
+        e0q = offsets[s0 + local];
+        Lq = offsets[s0 + local + 1] - e0q;
+      }
+      unsigned m = __ballot_sync(kFull, has);
+      while (m && !failed) {
+        const int r = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t ne0 = __shfl_sync(kFull, e0q, r), nL = __shfl_sync(kFull, Lq, r);
+        // stage segment number `issued`, then sort the previous one while it loads
+        if (lane == 0) rss_issue<K, kVals>(wbase, issued & 1, &bar[issued & 1], keys, vals, ne0, nL);
+        ++issued;
+        if (issued >= 2) sort_staged(issued - 2);
+        pe0 = ne0;
+        pL = nL;
       }
     }
   }
