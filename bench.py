@@ -66,6 +66,10 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch parameters instead of autotuning each segmented workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving loop")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the float-key and long-segment measurements")
+    ap.add_argument("--no-families", action="store_true",
+                    help="skip the network-family comparison (best known vs Bose-Nelson, u32 keys and 16-byte items)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson request stream")
     ap.add_argument("--serve-rate", type=float, default=20000.0, help="mean request arrival rate (1/s)")
     return ap.parse_args()
@@ -356,6 +360,10 @@ def bench_ours(args, rank, world, local_rank, dist):
     if not args.no_e2e:
         result["e2e"] = bench_e2e(args, sn, pristine, world, dist, device, parts)
     del work, graphs
+    if "sweep" in parts and not args.no_families:
+        result["network_families"] = bench_families(args, sn, pristine, device, dist)
+    if not args.no_extras:
+        result["extras"] = bench_extras(args, sn, device)
     if not args.no_plain:
         result["plain_vs_batched"] = bench_plain_vs_batched(args, sn, device, dist)
     if rank == 0 and world == 1 and not args.no_serving:
@@ -381,6 +389,117 @@ def capture_uneven(sn, w):
         sn.check(sn.sn_sort_segments_u64(w["uneven_keys"], w["uneven_vals"], w["uneven_off"]), "capture")
     torch.cuda.current_stream().wait_stream(stream)
     return graph
+
+
+# ------------------------------------------------------ network families ----
+
+def _time_calls(fn, restore, reps, warm):
+    """Mean CUDA-event time (ms) of fn() over `reps` runs, inputs restored before each."""
+    import torch
+    for _ in range(warm):
+        restore()
+        fn()
+    times = []
+    for _ in range(reps):
+        restore()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.mean(times)
+
+
+def bench_families(args, sn, pristine, device, dist):
+    """Best known networks vs Bose-Nelson (Sec. 2.2.1, 4.3) on GB300: the u32
+    sweep arrays (2^24 per n) and the paper's 16-byte items (u64 key + u64
+    reference) at 2^22 arrays per n.  Both are HBM-bound here, so the table
+    shows whether the extra comparators of Bose-Nelson cost anything."""
+    import torch
+    from paper_2002_05599_gb300 import workloads as wl
+    hbm, _ = peaks()
+    reps, warm = max(3, args.steps), max(3, args.warmup)
+    out = {"u32_sweep": {}, "items16": {}, "timing": "CUDA events, mean over repetitions, inputs restored"}
+    for n in SWEEP_NS:
+        src = pristine[f"sweep{n}"]
+        work = src.clone()
+        row = {}
+        for fam, name in ((sn.SN_NETWORK_BEST, "best"), (sn.SN_NETWORK_BOSE_NELSON, "bose_nelson")):
+            ms = _time_calls(lambda: sn.check(sn.sn_sort_fixed_family(work, n, fam)), lambda: work.copy_(src),
+                             reps, warm)
+            row[name] = {"ms": round(ms, 4), "gkeys_s": round(src.numel() / (ms * 1e-3) / 1e9, 1),
+                         "frac_hbm": round(8 * src.numel() / (ms * 1e-3) / 1e9 / hbm, 4)}
+        out["u32_sweep"][n] = row
+        del work
+    count = (1 << 22) >> args.scale
+    for n in (2, 4, 8, 12, 16):
+        keys = wl.uniform_keys_torch(count * n, np.uint64, seed=500 + n, device=device)
+        src = torch.stack([keys, torch.arange(count * n, dtype=torch.int64, device=device)], 1).reshape(-1)
+        work = src.clone()
+        row = {}
+        for fam, name in ((sn.SN_NETWORK_BEST, "best"), (sn.SN_NETWORK_BOSE_NELSON, "bose_nelson")):
+            ms = _time_calls(lambda: sn.check(sn.sn_sort_fixed_items(work, n, fam)), lambda: work.copy_(src),
+                             reps, warm)
+            row[name] = {"ms": round(ms, 4), "gitems_s": round(count * n / (ms * 1e-3) / 1e9, 1),
+                         "frac_hbm": round(32 * count * n / (ms * 1e-3) / 1e9 / hbm, 4)}
+        out["items16"][n] = row
+        del keys, src, work
+    sn.check(sn.sn_check(), "network families")
+    out["items16_arrays_per_n"] = count
+    return out
+
+
+# --------------------------------------------- float keys, long segments ----
+
+def bench_extras(args, sn, device):
+    """Float keys next to the same-width unsigned keys (the order-preserving
+    code runs in registers, so both should cost the same), and segments of
+    257..4096 items (sn_sort_segments_large)."""
+    import torch
+    from paper_2002_05599_gb300 import workloads as wl
+    hbm, _ = peaks()
+    reps, warm = max(3, args.steps), max(3, args.warmup)
+    out = {"timing": "CUDA events, mean over repetitions, inputs restored"}
+    count = (1 << 24) >> args.scale
+    fixed = {}
+    for n in (8, 16):
+        src = wl.uniform_keys_torch(count * n, np.uint32, seed=700 + n, device=device)
+        work = src.clone()
+        row = {}
+        for name, fn in (("u32", sn.sn_sort_fixed), ("f32", sn.sn_sort_fixed_f32)):
+            ms = _time_calls(lambda: sn.check(fn(work, n)), lambda: work.copy_(src), reps, warm)
+            row[name] = {"ms": round(ms, 4), "gkeys_s": round(count * n / (ms * 1e-3) / 1e9, 1),
+                         "frac_hbm": round(8 * count * n / (ms * 1e-3) / 1e9 / hbm, 4)}
+        fixed[n] = row
+        del src, work
+    out["fixed_2^24_arrays"] = fixed
+    nseg = (1 << 20) >> args.scale
+    lens = wl.segment_lengths(nseg, "uniform", seed=701, lo=2, hi=256)
+    off = wl.offsets_from_lengths(lens)
+    d_off = torch.from_numpy(off.view(np.int32)).to(device)
+    src = wl.uniform_keys_torch(int(off[-1]), np.uint32, seed=701, device=device)
+    work = src.clone()
+    row = {}
+    for name, fn in (("u32", sn.sn_sort_segments), ("f32", sn.sn_sort_segments_f32)):
+        ms = _time_calls(lambda: sn.check(fn(work, None, d_off)), lambda: work.copy_(src), reps, warm)
+        row[name] = {"ms": round(ms, 4), "gkeys_s": round(src.numel() / (ms * 1e-3) / 1e9, 1)}
+    out["segments_2^20_uniform_2..256_keys_only"] = row
+    del src, work
+    nseg = (1 << 16) >> args.scale
+    lens = wl.segment_lengths(nseg, "uniform", seed=702, lo=257, hi=4096)
+    off = wl.offsets_from_lengths(lens)
+    d_off = torch.from_numpy(off.view(np.int32)).to(device)
+    for dt, name, fn in ((np.uint32, "u32_keys_only", sn.sn_sort_segments_large),
+                         (np.uint64, "u64_keys_only", sn.sn_sort_segments_large_u64)):
+        src = wl.uniform_keys_torch(int(off[-1]), dt, seed=702, device=device)
+        work = src.clone()
+        ms = _time_calls(lambda: sn.check(fn(work, None, d_off)), lambda: work.copy_(src), reps, warm)
+        out.setdefault(f"large_{nseg}_segments_257..4096", {})[name] = {
+            "ms": round(ms, 4), "gkeys_s": round(src.numel() / (ms * 1e-3) / 1e9, 1)}
+        del src, work
+    sn.check(sn.sn_check(), "extras")
+    return out
 
 
 # ------------------------------------------------- plain vs batched ---------

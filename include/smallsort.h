@@ -64,6 +64,48 @@ int sn_sort_fixed(uint32_t *keys, int n, uint64_t count, sn_stream_t stream);
 int sn_sort_fixed_u64(uint64_t *keys, int n, uint64_t count, sn_stream_t stream);
 
 /*
+ * Network families for the fixed-size calls (Sec. 2.2.1): the best known
+ * networks (sizes 1, 3, 5, 9, 12, 16, 19, 25, 29, 35, 39, 46, 51, 56, 60 for
+ * n = 2..16), or Bose and Nelson's recursive construction (BN-L of the paper:
+ * 65 comparators at n = 16).  Both sort every input; they differ in size,
+ * depth and locality only.
+ */
+#define SN_NETWORK_BEST 0
+#define SN_NETWORK_BOSE_NELSON 1
+
+/* sn_sort_fixed with a choice of network family (SN_EINVAL for another value). */
+int sn_sort_fixed_family(uint32_t *keys, int n, uint64_t count, int family, sn_stream_t stream);
+
+/*
+ * The paper's item type (Sec. 4.1: a 64-bit key and a 64-bit reference that
+ * travels with it, 16 bytes), in `count` contiguous arrays of n items
+ * (array-of-structs, the ArrayInRow layout).  Each array is sorted in place
+ * by key; items with equal keys keep their order in the array, so the result
+ * is unique.  Same n, count and alignment rules as sn_sort_fixed (items must
+ * be 8-byte aligned; 16-byte-aligned arrays take the bulk-copy path).
+ */
+typedef struct {
+    uint64_t key;
+    uint64_t ref;
+} sn_item64;
+int sn_sort_fixed_items(sn_item64 *items, int n, uint64_t count, int family, sn_stream_t stream);
+
+/*
+ * Floating-point keys: the same calls for IEEE-754 single and double keys,
+ * ordered by the standard's totalOrder: -NaN < -inf < negative numbers < -0
+ * < +0 < positive numbers < +inf < +NaN (NaNs ordered by their payload
+ * bits).  Keys are sorted as their bit patterns through an order-preserving
+ * code applied in registers, so the bits of every key come back unchanged.
+ * Conventions as for the u32 / u64 calls (payload ties by original position).
+ */
+int sn_sort_fixed_f32(float *keys, int n, uint64_t count, sn_stream_t stream);
+int sn_sort_fixed_f64(double *keys, int n, uint64_t count, sn_stream_t stream);
+int sn_sort_segments_f32(float *keys, uint32_t *vals, const uint32_t *offsets, uint64_t nseg,
+                         sn_stream_t stream);
+int sn_sort_segments_f64(double *keys, uint32_t *vals, const uint32_t *offsets, uint64_t nseg,
+                         sn_stream_t stream);
+
+/*
  * CSR segments (spec batching layer; the paper's Sec. 5 suggests
  * bucketing base cases by size and solving batches of equal size).
  *
@@ -170,6 +212,23 @@ int sn_tune_segments(void *keys, uint32_t *vals, const uint32_t *offsets, uint64
  */
 int sn_tuning_save(const char *path);
 int sn_tuning_load(const char *path);
+
+/*
+ * Segments longer than 256 items (library addition; the paper names merging
+ * networks as the way beyond its 256-item range, Sec. 5).  Same contract as
+ * sn_sort_segments / _u64, for lengths 0..SN_MAX_SEGMENT_LARGE: one thread
+ * block per segment sorts the (key, position) items in shared memory with the
+ * bitonic sorting network on the next power of two channels.  A length above
+ * the limit or decreasing offsets are detected on the device first: keys and
+ * payload stay untouched and sn_check() reports SN_ERANGE.  Meant for batches
+ * of long segments; batches of segments <= 256 are faster through
+ * sn_sort_segments.  Scratch: one device word from the library's pool.
+ */
+#define SN_MAX_SEGMENT_LARGE 4096
+int sn_sort_segments_large(uint32_t *keys, uint32_t *vals, const uint32_t *offsets, uint64_t nseg,
+                           sn_stream_t stream);
+int sn_sort_segments_large_u64(uint64_t *keys, uint32_t *vals, const uint32_t *offsets, uint64_t nseg,
+                               sn_stream_t stream);
 
 /*
  * Synchronises `stream`, then returns and clears the device status word of the

@@ -11,6 +11,11 @@ Sets of Items".  What each function follows:
 * ``sort_fixed``      -- Sec. 2.1 (a network's output is the input permutation
   in non-decreasing order) computed by insertion sort "IS Def" (Sec. 4.2), one
   array after another as in the ArrayInRow layout (Sec. 4.1).
+* float32 / float64 keys (``sort_fixed``, ``sort_segments``) -- ordered by
+  IEEE 754 totalOrder, written case by case from its definition (library
+  addition: the paper's keys are integers).
+* ``sort_fixed_items`` -- the same for the paper's 16-byte items (u64 key,
+  u64 reference, Sec. 4.1), stable by key.
 * ``sort_segments``   -- per-segment stable insertion sort; payload values move
   with their keys like the reference values of Sec. 2.2.1.  Ties keep input
   order: the (key, original position) reading of this library.
@@ -59,7 +64,13 @@ def _load():
     for name in ("oracle_sort_fixed_u32", "oracle_sort_fixed_u64"):
         getattr(lib, name).argtypes = [P, I, U64]
         getattr(lib, name).restype = None
-    for name in ("oracle_sort_segments_u32", "oracle_sort_segments_u64"):
+    for name in ("oracle_sort_fixed_f32", "oracle_sort_fixed_f64"):
+        getattr(lib, name).argtypes = [P, I, U64]
+        getattr(lib, name).restype = None
+    lib.oracle_sort_fixed_items.argtypes = [P, I, U64]
+    lib.oracle_sort_fixed_items.restype = None
+    for name in ("oracle_sort_segments_u32", "oracle_sort_segments_u64", "oracle_sort_segments_f32",
+                 "oracle_sort_segments_f64"):
         getattr(lib, name).argtypes = [P, P, P, U64]
         getattr(lib, name).restype = None
     for name in ("oracle_network_failures_01", "oracle_network_failures_perm",
@@ -90,8 +101,20 @@ def sort_fixed(keys: np.ndarray, n: int) -> np.ndarray:
     if out.size % n:
         raise ValueError("size is not a multiple of n")
     fn = {np.dtype(np.uint32): lib.oracle_sort_fixed_u32,
-          np.dtype(np.uint64): lib.oracle_sort_fixed_u64}[out.dtype]
+          np.dtype(np.uint64): lib.oracle_sort_fixed_u64,
+          np.dtype(np.float32): lib.oracle_sort_fixed_f32,
+          np.dtype(np.float64): lib.oracle_sort_fixed_f64}[out.dtype]
     fn(_ptr(out), n, out.size // n)
+    return out
+
+
+def sort_fixed_items(items: np.ndarray, n: int) -> np.ndarray:
+    """Return a copy of ``items`` (u64, interleaved key, ref of ``count*n``
+    items) with each array of ``n`` items sorted by key, stably (Sec. 4.1)."""
+    out = np.ascontiguousarray(items, dtype=np.uint64).copy()
+    if out.size % (2 * n):
+        raise ValueError("size is not a multiple of 2n")
+    _load().oracle_sort_fixed_items(_ptr(out), n, out.size // (2 * n))
     return out
 
 
@@ -103,7 +126,9 @@ def sort_segments(keys: np.ndarray, vals, offsets: np.ndarray):
     v = None if vals is None else np.ascontiguousarray(vals, dtype=np.uint32).copy()
     off = np.ascontiguousarray(offsets, dtype=np.uint32)
     fn = {np.dtype(np.uint32): lib.oracle_sort_segments_u32,
-          np.dtype(np.uint64): lib.oracle_sort_segments_u64}[k.dtype]
+          np.dtype(np.uint64): lib.oracle_sort_segments_u64,
+          np.dtype(np.float32): lib.oracle_sort_segments_f32,
+          np.dtype(np.float64): lib.oracle_sort_segments_f64}[k.dtype]
     fn(_ptr(k), _ptr(v), _ptr(off), off.size - 1)
     return k, v
 

@@ -22,7 +22,9 @@
  *   - the paper's probabilistic permutation check (Sec. 4.1,
  *     "Checking Results: Permutation Check").
  */
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 #include <stddef.h>
 
 /* ---- Sorting: insertion sort "IS Def" (Sec. 4.2, textbook, array indices) ---- */
@@ -56,6 +58,30 @@ void oracle_sort_fixed_u64(uint64_t *keys, int n, uint64_t count)
                 --j;
             }
             A[j + 1] = x;
+        }
+    }
+}
+
+/*
+ * The 16-byte items of the paper's experiments (Sec. 4.1: a 64-bit key and a
+ * 64-bit reference), `count` arrays of n items stored as key, ref, key, ref,
+ * ...  Each array is sorted by key with insertion sort; the reference moves
+ * with its key and equal keys keep their input order.
+ */
+void oracle_sort_fixed_items(uint64_t *items, int n, uint64_t count)
+{
+    for (uint64_t a = 0; a < count; ++a) {
+        uint64_t *A = items + 2 * a * (uint64_t)n;
+        for (int i = 1; i < n; ++i) {
+            uint64_t key = A[2 * i], ref = A[2 * i + 1];
+            int j = i - 1;
+            while (j >= 0 && A[2 * j] > key) {
+                A[2 * (j + 1)] = A[2 * j];
+                A[2 * (j + 1) + 1] = A[2 * j + 1];
+                --j;
+            }
+            A[2 * (j + 1)] = key;
+            A[2 * (j + 1) + 1] = ref;
         }
     }
 }
@@ -100,6 +126,133 @@ void oracle_sort_segments_u64(uint64_t *keys, uint32_t *vals,
             uint32_t v = V ? V[i] : 0;
             int64_t j = i - 1;
             while (j >= 0 && A[j] > x) {
+                A[j + 1] = A[j];
+                if (V) V[j + 1] = V[j];
+                --j;
+            }
+            A[j + 1] = x;
+            if (V) V[j + 1] = v;
+        }
+    }
+}
+
+/* ---- Floating-point keys: IEEE 754 totalOrder ---- */
+
+/*
+ * greater(a, b): a follows b in the totalOrder of IEEE 754 (Sec. 5.10 of the
+ * standard), written case by case from its definition rather than from a
+ * bit encoding:
+ *   - numbers (and infinities) compare by value;
+ *   - -0 precedes +0;
+ *   - a NaN with the sign bit set precedes every non-NaN, one without it
+ *     follows every non-NaN;
+ *   - two NaNs of the same sign: for positive NaNs the smaller payload (the
+ *     bits below the sign) comes first, for negative NaNs the larger.
+ * Identical bit patterns are not greater than each other.
+ */
+static int nan_class(int isnan_, int neg)
+{
+    return isnan_ ? (neg ? -1 : 1) : 0;
+}
+
+static int greater_f64(double a, double b)
+{
+    int ca = nan_class(isnan(a), signbit(a) != 0), cb = nan_class(isnan(b), signbit(b) != 0);
+    if (ca != cb) return ca > cb;
+    if (ca == 0) {
+        if (a != b) return a > b;
+        return (signbit(a) == 0) && (signbit(b) != 0); /* +0 after -0 */
+    }
+    uint64_t pa, pb;
+    memcpy(&pa, &a, 8);
+    memcpy(&pb, &b, 8);
+    pa &= 0x7FFFFFFFFFFFFFFFull;
+    pb &= 0x7FFFFFFFFFFFFFFFull;
+    return ca > 0 ? pa > pb : pa < pb;
+}
+
+static int greater_f32(float a, float b)
+{
+    int ca = nan_class(isnan(a), signbit(a) != 0), cb = nan_class(isnan(b), signbit(b) != 0);
+    if (ca != cb) return ca > cb;
+    if (ca == 0) {
+        if (a != b) return a > b;
+        return (signbit(a) == 0) && (signbit(b) != 0);
+    }
+    uint32_t pa, pb;
+    memcpy(&pa, &a, 4);
+    memcpy(&pb, &b, 4);
+    pa &= 0x7FFFFFFFu;
+    pb &= 0x7FFFFFFFu;
+    return ca > 0 ? pa > pb : pa < pb;
+}
+
+/* Arrays of n keys, insertion sort by totalOrder (stable). */
+void oracle_sort_fixed_f32(float *keys, int n, uint64_t count)
+{
+    for (uint64_t a = 0; a < count; ++a) {
+        float *A = keys + a * (uint64_t)n;
+        for (int i = 1; i < n; ++i) {
+            float x = A[i];
+            int j = i - 1;
+            while (j >= 0 && greater_f32(A[j], x)) {
+                A[j + 1] = A[j];
+                --j;
+            }
+            A[j + 1] = x;
+        }
+    }
+}
+
+void oracle_sort_fixed_f64(double *keys, int n, uint64_t count)
+{
+    for (uint64_t a = 0; a < count; ++a) {
+        double *A = keys + a * (uint64_t)n;
+        for (int i = 1; i < n; ++i) {
+            double x = A[i];
+            int j = i - 1;
+            while (j >= 0 && greater_f64(A[j], x)) {
+                A[j + 1] = A[j];
+                --j;
+            }
+            A[j + 1] = x;
+        }
+    }
+}
+
+/* CSR segments by totalOrder, stable, payload moved with its key. */
+void oracle_sort_segments_f32(float *keys, uint32_t *vals, const uint32_t *offsets, uint64_t nseg)
+{
+    for (uint64_t s = 0; s < nseg; ++s) {
+        float *A = keys + offsets[s];
+        uint32_t *V = vals ? vals + offsets[s] : NULL;
+        int64_t len = (int64_t)offsets[s + 1] - (int64_t)offsets[s];
+        for (int64_t i = 1; i < len; ++i) {
+            float x = A[i];
+            uint32_t v = V ? V[i] : 0;
+            int64_t j = i - 1;
+            while (j >= 0 && greater_f32(A[j], x)) {
+                A[j + 1] = A[j];
+                if (V) V[j + 1] = V[j];
+                --j;
+            }
+            A[j + 1] = x;
+            if (V) V[j + 1] = v;
+        }
+    }
+}
+
+void oracle_sort_segments_f64(double *keys, uint32_t *vals, const uint32_t *offsets, uint64_t nseg)
+{
+    for (uint64_t s = 0; s < nseg; ++s) {
+        double *A = keys + offsets[s];
+        uint32_t *V = vals ? vals + offsets[s] : NULL;
+        int64_t len = (int64_t)offsets[s + 1] - (int64_t)offsets[s];
+        for (int64_t i = 1; i < len; ++i) {
+            double x = A[i];
+            uint32_t v = V ? V[i] : 0;
+            int64_t j = i - 1;
+            while (j >= 0 && greater_f64(A[j], x)) {
                 A[j + 1] = A[j];
                 if (V) V[j + 1] = V[j];
                 --j;

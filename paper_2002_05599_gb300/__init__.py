@@ -17,6 +17,9 @@ from ._binding import (  # noqa: F401
     SN_ECUDA,
     SN_ETIMEOUT,
     SN_EUNSUPPORTED,
+    SN_MAX_SEGMENT_LARGE,
+    SN_NETWORK_BEST,
+    SN_NETWORK_BOSE_NELSON,
     SN_OK,
     SmallSortError,
     SnTuning,
@@ -27,8 +30,16 @@ from ._binding import (  # noqa: F401
     rss_sort_segments_u64,
     sn_check,
     sn_sort_fixed,
+    sn_sort_fixed_f32,
+    sn_sort_fixed_f64,
+    sn_sort_fixed_family,
+    sn_sort_fixed_items,
     sn_sort_fixed_u64,
     sn_sort_segments,
+    sn_sort_segments_f32,
+    sn_sort_segments_f64,
+    sn_sort_segments_large,
+    sn_sort_segments_large_u64,
     sn_sort_segments_u64,
     sn_status_string,
     sn_tune_segments,

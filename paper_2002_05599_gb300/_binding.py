@@ -45,6 +45,17 @@ def library():
     P, U64, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
     lib.sn_sort_fixed.argtypes = [P, I, U64, P]
     lib.sn_sort_fixed_u64.argtypes = [P, I, U64, P]
+    lib.sn_sort_fixed_family.argtypes = [P, I, U64, I, P]
+    lib.sn_sort_fixed_items.argtypes = [P, I, U64, I, P]
+    lib.sn_sort_fixed_family.restype = I
+    lib.sn_sort_fixed_items.restype = I
+    for name in ("sn_sort_fixed_f32", "sn_sort_fixed_f64"):
+        getattr(lib, name).argtypes = [P, I, U64, P]
+        getattr(lib, name).restype = I
+    for name in ("sn_sort_segments_f32", "sn_sort_segments_f64", "sn_sort_segments_large",
+                 "sn_sort_segments_large_u64"):
+        getattr(lib, name).argtypes = [P, P, P, U64, P]
+        getattr(lib, name).restype = I
     for name in ("sn_sort_segments", "sn_sort_segments_u64",
                  "rss_sort_segments", "rss_sort_segments_u64"):
         getattr(lib, name).argtypes = [P, P, P, U64, P]
@@ -97,6 +108,60 @@ def sn_sort_fixed_u64(keys, n: int, count: int | None = None, stream=None) -> in
     if count is None:
         count = _elems(keys, 8) // n
     return library().sn_sort_fixed_u64(_addr(keys), n, count, _stream(stream))
+
+
+SN_NETWORK_BEST = 0
+SN_NETWORK_BOSE_NELSON = 1
+
+
+def sn_sort_fixed_family(keys, n: int, family: int, count: int | None = None, stream=None) -> int:
+    """sn_sort_fixed with a network family (SN_NETWORK_BEST / SN_NETWORK_BOSE_NELSON)."""
+    if count is None:
+        count = _elems(keys, 4) // n
+    return library().sn_sort_fixed_family(_addr(keys), n, count, family, _stream(stream))
+
+
+def sn_sort_fixed_items(items, n: int, family: int = SN_NETWORK_BEST, count: int | None = None,
+                        stream=None) -> int:
+    """Sort ``count`` arrays of ``n`` 16-byte items (u64 key, u64 ref; a 64-bit
+    tensor of 2*count*n elements, key and ref interleaved) by key, in place."""
+    if count is None:
+        count = _elems(items, 8) // (2 * n)
+    return library().sn_sort_fixed_items(_addr(items), n, count, family, _stream(stream))
+
+
+def sn_sort_fixed_f32(keys, n: int, count: int | None = None, stream=None) -> int:
+    """Sort ``count`` arrays of ``n`` float32 keys in place (IEEE 754 totalOrder)."""
+    if count is None:
+        count = _elems(keys, 4) // n
+    return library().sn_sort_fixed_f32(_addr(keys), n, count, _stream(stream))
+
+
+def sn_sort_fixed_f64(keys, n: int, count: int | None = None, stream=None) -> int:
+    """Sort ``count`` arrays of ``n`` float64 keys in place (IEEE 754 totalOrder)."""
+    if count is None:
+        count = _elems(keys, 8) // n
+    return library().sn_sort_fixed_f64(_addr(keys), n, count, _stream(stream))
+
+
+def sn_sort_segments_f32(keys, vals, offsets, nseg: int | None = None, stream=None) -> int:
+    return _segments(library().sn_sort_segments_f32, 4, keys, vals, offsets, nseg, stream)
+
+
+def sn_sort_segments_f64(keys, vals, offsets, nseg: int | None = None, stream=None) -> int:
+    return _segments(library().sn_sort_segments_f64, 8, keys, vals, offsets, nseg, stream)
+
+
+SN_MAX_SEGMENT_LARGE = 4096
+
+
+def sn_sort_segments_large(keys, vals, offsets, nseg: int | None = None, stream=None) -> int:
+    """Segments of up to SN_MAX_SEGMENT_LARGE u32 keys (one thread block per segment)."""
+    return _segments(library().sn_sort_segments_large, 4, keys, vals, offsets, nseg, stream)
+
+
+def sn_sort_segments_large_u64(keys, vals, offsets, nseg: int | None = None, stream=None) -> int:
+    return _segments(library().sn_sort_segments_large_u64, 8, keys, vals, offsets, nseg, stream)
 
 
 def _segments(fn, ksize, keys, vals, offsets, nseg, stream):

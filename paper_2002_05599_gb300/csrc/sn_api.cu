@@ -78,17 +78,19 @@ const DeviceInfo* device_info(int* err) {
 namespace {
 
 template <class K>
-int fixed_entry(K* keys, int n, uint64_t count, sn_stream_t stream,
-                cudaError_t (*launch)(K*, int, uint64_t, cudaStream_t, const sn::DeviceInfo&)) {
+int fixed_entry(K* keys, int n, uint64_t count, int family, sn_stream_t stream,
+                cudaError_t (*launch)(K*, int, uint64_t, int, cudaStream_t, const sn::DeviceInfo&)) {
   if (n < 2 || n > 16) return SN_EINVAL;
+  if (family != SN_NETWORK_BEST && family != SN_NETWORK_BOSE_NELSON) return SN_EINVAL;
   if (count == 0) return SN_OK;
   if (keys == nullptr) return SN_EINVAL;
   if (count > (1ull << 62) / static_cast<uint64_t>(n)) return SN_ERANGE;
-  if (reinterpret_cast<uintptr_t>(keys) % sizeof(K) != 0) return SN_EINVAL;
+  if (reinterpret_cast<uintptr_t>(keys) % (sizeof(K) < 8 ? sizeof(K) : 8) != 0) return SN_EINVAL;
   int err = SN_OK;
   const sn::DeviceInfo* d = sn::device_info(&err);
   if (d == nullptr) return err;
-  return launch(keys, n, count, reinterpret_cast<cudaStream_t>(stream), *d) == cudaSuccess ? SN_OK : SN_ECUDA;
+  return launch(keys, n, count, family, reinterpret_cast<cudaStream_t>(stream), *d) == cudaSuccess ? SN_OK
+                                                                                                  : SN_ECUDA;
 }
 
 template <class K>
@@ -128,6 +130,37 @@ int segments_entry(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t ns
   return e == cudaSuccess ? SN_OK : SN_ECUDA;
 }
 
+template <class K>
+int large_entry(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream,
+                cudaError_t (*launch)(K*, uint32_t*, const uint32_t*, uint64_t, void*, cudaStream_t,
+                                      const sn::DeviceInfo&)) {
+  if (nseg == 0) return SN_OK;
+  if (keys == nullptr || offsets == nullptr) return SN_EINVAL;
+  if (nseg >= (1ull << 32)) return SN_ERANGE;
+  if (reinterpret_cast<uintptr_t>(keys) % sizeof(K) != 0 || reinterpret_cast<uintptr_t>(offsets) % 4 != 0 ||
+      reinterpret_cast<uintptr_t>(vals) % 4 != 0)
+    return SN_EINVAL;
+  int err = SN_OK;
+  const sn::DeviceInfo* d = sn::device_info(&err);
+  if (d == nullptr) return err;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* scratch = nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return SN_ECUDA;
+  }
+  const cudaError_t ae = cap == cudaStreamCaptureStatusActive ? cudaMallocAsync(&scratch, 256, s)
+                                                              : cudaMallocFromPoolAsync(&scratch, 256, d->pool, s);
+  if (ae != cudaSuccess) {
+    cudaGetLastError();
+    return SN_ENOMEM;
+  }
+  const cudaError_t e = launch(keys, vals, offsets, nseg, scratch, s, *d);
+  cudaFreeAsync(scratch, s);
+  return e == cudaSuccess ? SN_OK : SN_ECUDA;
+}
+
 }  // namespace
 
 namespace sn {
@@ -141,11 +174,27 @@ size_t segments_scratch_bytes(uint64_t nseg, const SegTuning& t) {
 extern "C" {
 
 int sn_sort_fixed(uint32_t* keys, int n, uint64_t count, sn_stream_t stream) {
-  return fixed_entry<uint32_t>(keys, n, count, stream, sn::launch_fixed_u32);
+  return fixed_entry<uint32_t>(keys, n, count, SN_NETWORK_BEST, stream, sn::launch_fixed_u32);
 }
 
 int sn_sort_fixed_u64(uint64_t* keys, int n, uint64_t count, sn_stream_t stream) {
-  return fixed_entry<uint64_t>(keys, n, count, stream, sn::launch_fixed_u64);
+  return fixed_entry<uint64_t>(keys, n, count, SN_NETWORK_BEST, stream, sn::launch_fixed_u64);
+}
+
+int sn_sort_fixed_family(uint32_t* keys, int n, uint64_t count, int family, sn_stream_t stream) {
+  return fixed_entry<uint32_t>(keys, n, count, family, stream, sn::launch_fixed_u32);
+}
+
+int sn_sort_fixed_items(sn_item64* items, int n, uint64_t count, int family, sn_stream_t stream) {
+  return fixed_entry<sn_item64>(items, n, count, family, stream, sn::launch_fixed_items);
+}
+
+int sn_sort_fixed_f32(float* keys, int n, uint64_t count, sn_stream_t stream) {
+  return fixed_entry<float>(keys, n, count, SN_NETWORK_BEST, stream, sn::launch_fixed_f32);
+}
+
+int sn_sort_fixed_f64(double* keys, int n, uint64_t count, sn_stream_t stream) {
+  return fixed_entry<double>(keys, n, count, SN_NETWORK_BEST, stream, sn::launch_fixed_f64);
 }
 
 int sn_sort_segments(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream) {
@@ -157,6 +206,26 @@ int sn_sort_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets
                          sn_stream_t stream) {
   return segments_entry<uint64_t>(keys, vals, offsets, nseg, stream, sn::SegMode::kNetworkWarpRss,
                                   sn::launch_segments_u64);
+}
+
+int sn_sort_segments_f32(float* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream) {
+  return segments_entry<float>(keys, vals, offsets, nseg, stream, sn::SegMode::kNetworkWarpRss,
+                               sn::launch_segments_f32);
+}
+
+int sn_sort_segments_f64(double* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream) {
+  return segments_entry<double>(keys, vals, offsets, nseg, stream, sn::SegMode::kNetworkWarpRss,
+                                sn::launch_segments_f64);
+}
+
+int sn_sort_segments_large(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
+                           sn_stream_t stream) {
+  return large_entry<uint32_t>(keys, vals, offsets, nseg, stream, sn::launch_large_u32);
+}
+
+int sn_sort_segments_large_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
+                               sn_stream_t stream) {
+  return large_entry<uint64_t>(keys, vals, offsets, nseg, stream, sn::launch_large_u64);
 }
 
 int rss_sort_segments(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream) {

@@ -96,6 +96,29 @@ __device__ __forceinline__ Item64 pick(const Item64& mine, const Item64& other, 
 
 // -------------------------------------------------------- networks --------
 
+// Order-preserving codes of IEEE-754 bit patterns held as unsigned words:
+// negative values get all bits flipped, non-negative ones the sign bit set, so
+// the unsigned order of the codes is the standard's totalOrder (-NaN < -inf <
+// ... < -0 < +0 < ... < +inf < +NaN).  Identity for integer keys (kF false).
+template <class K, bool kF>
+__device__ __forceinline__ K key_enc(K x) {
+  if constexpr (kF) {
+    constexpr K top = static_cast<K>(1) << (8 * sizeof(K) - 1);
+    return (x & top) ? static_cast<K>(~x) : static_cast<K>(x | top);
+  } else {
+    return x;
+  }
+}
+template <class K, bool kF>
+__device__ __forceinline__ K key_dec(K x) {
+  if constexpr (kF) {
+    constexpr K top = static_cast<K>(1) << (8 * sizeof(K) - 1);
+    return (x & top) ? static_cast<K>(x & ~top) : static_cast<K>(~x);
+  } else {
+    return x;
+  }
+}
+
 // Net<N>::run applies the generated N-channel network to a register array.
 template <int N> struct Net;
 template <> struct Net<0> {
@@ -127,6 +150,32 @@ SN_DEFINE_NET(14)
 SN_DEFINE_NET(15)
 SN_DEFINE_NET(16)
 #undef SN_DEFINE_NET
+
+// NetBN<N>::run applies Bose and Nelson's recursively constructed N-channel
+// network (the family the paper compares against the best known networks).
+template <int N> struct NetBN;
+#define SN_DEFINE_BN(n)                                           \
+  template <> struct NetBN<n> {                                   \
+    template <class T> __device__ __forceinline__ static void run(T* k) { \
+      SN_BN_##n(SN_CE_)                                           \
+    }                                                             \
+  };
+SN_DEFINE_BN(2)
+SN_DEFINE_BN(3)
+SN_DEFINE_BN(4)
+SN_DEFINE_BN(5)
+SN_DEFINE_BN(6)
+SN_DEFINE_BN(7)
+SN_DEFINE_BN(8)
+SN_DEFINE_BN(9)
+SN_DEFINE_BN(10)
+SN_DEFINE_BN(11)
+SN_DEFINE_BN(12)
+SN_DEFINE_BN(13)
+SN_DEFINE_BN(14)
+SN_DEFINE_BN(15)
+SN_DEFINE_BN(16)
+#undef SN_DEFINE_BN
 #undef SN_CE_
 
 // ------------------------------------------------ warp shuffles -----------
@@ -150,6 +199,15 @@ __device__ __forceinline__ void warp_network32(T& x, int lane) {
 #define SN_WARP_STEP_(M) { const T o = shfl_xor(x, M); x = pick(x, o, lane < (lane ^ (M))); }
   SN_WARP32_SCHEDULE(SN_WARP_STEP_)
 #undef SN_WARP_STEP_
+}
+
+// Comparator `c` of the step with XOR mask `mask` of the ascending bitonic
+// sorter (mask = k-1 for the mirrored first step of a merge of size k, else a
+// power of two): returns the lower slot; the partner is slot ^ mask.
+__device__ __forceinline__ int bitonic_slot(int c, int mask) {
+  const int h = (mask & (mask + 1)) == 0 ? (mask + 1) >> 1 : mask;  // highest bit of the pair distance
+  const int b = __ffs(h) - 1;
+  return ((c >> b) << (b + 1)) | (c & (h - 1));
 }
 
 // ------------------------------------------------ async-proxy PTX ---------

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "smallsort.h"
+
 namespace sn {
 
 struct DeviceInfo {
@@ -18,9 +20,17 @@ struct DeviceInfo {
 // Per-device facts, initialised once per device (thread-safe).
 const DeviceInfo* device_info(int* err);
 
-// Fixed-size arrays (sn_fixed.cu).  Return a cudaError_t.
-cudaError_t launch_fixed_u32(uint32_t* keys, int n, uint64_t count, cudaStream_t s, const DeviceInfo& d);
-cudaError_t launch_fixed_u64(uint64_t* keys, int n, uint64_t count, cudaStream_t s, const DeviceInfo& d);
+// Fixed-size arrays (sn_fixed_*.cu; kernels in sn_fixed.cuh).  `family` is
+// SN_NETWORK_BEST or SN_NETWORK_BOSE_NELSON (u64 keys: best only).  Return a
+// cudaError_t.
+cudaError_t launch_fixed_u32(uint32_t* keys, int n, uint64_t count, int family, cudaStream_t s,
+                             const DeviceInfo& d);
+cudaError_t launch_fixed_u64(uint64_t* keys, int n, uint64_t count, int family, cudaStream_t s,
+                             const DeviceInfo& d);
+cudaError_t launch_fixed_items(sn_item64* items, int n, uint64_t count, int family, cudaStream_t s,
+                               const DeviceInfo& d);
+cudaError_t launch_fixed_f32(float* keys, int n, uint64_t count, int family, cudaStream_t s, const DeviceInfo& d);
+cudaError_t launch_fixed_f64(double* keys, int n, uint64_t count, int family, cudaStream_t s, const DeviceInfo& d);
 
 // Segments (sn_segments.cu).
 enum class SegMode : int { kNetworkWarpRss = 0, kRssOnly = 1 };
@@ -54,5 +64,19 @@ cudaError_t launch_segments_u32(uint32_t* keys, uint32_t* vals, const uint32_t* 
 cudaError_t launch_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
                                 SegMode mode, void* scratch, size_t scratch_bytes, const SegTuning& t,
                                 cudaStream_t s, const DeviceInfo& d);
+// Segments of up to SN_MAX_SEGMENT_LARGE items, one CTA per segment
+// (sn_large.cu); `scratch` holds one device word (the validation flag).
+cudaError_t launch_large_u32(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, void* scratch,
+                             cudaStream_t s, const DeviceInfo& d);
+cudaError_t launch_large_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, void* scratch,
+                             cudaStream_t s, const DeviceInfo& d);
+
+// f32 / f64 keys, ordered by IEEE-754 totalOrder (sn_segments_f32.cu / _f64.cu).
+cudaError_t launch_segments_f32(float* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,
+                                void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
+                                const DeviceInfo& d);
+cudaError_t launch_segments_f64(double* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,
+                                void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
+                                const DeviceInfo& d);
 
 }  // namespace sn

@@ -239,13 +239,13 @@ __global__ void __launch_bounds__(256)
 
 // Segment of L <= N items at kbuf[p..p+L), padded with +inf to N channels
 // (payload at vbuf[pv..pv+L)).
-template <int N, class K, bool kVals>
+template <int N, class K, bool kVals, bool kF>
 __device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L) {
   if constexpr (kVals) {
     using IO = ItemOf<K>;
     typename IO::T it[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) it[q] = q < L ? IO::make(kbuf[p + q], q) : IO::sentinel(q);
+    for (int q = 0; q < N; ++q) it[q] = q < L ? IO::make(key_enc<K, kF>(kbuf[p + q]), q) : IO::sentinel(q);
     Net<N>::run(it);
     uint32_t v[N];
 #pragma unroll
@@ -254,18 +254,18 @@ __device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int 
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       if (q < L) {
-        kbuf[p + q] = IO::key(it[q]);
+        kbuf[p + q] = key_dec<K, kF>(IO::key(it[q]));
         vbuf[pv + q] = v[q];
       }
     }
   } else {
     K k[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) k[q] = q < L ? kbuf[p + q] : static_cast<K>(~static_cast<K>(0));
+    for (int q = 0; q < N; ++q) k[q] = q < L ? key_enc<K, kF>(kbuf[p + q]) : static_cast<K>(~static_cast<K>(0));
     Net<N>::run(k);
 #pragma unroll
     for (int q = 0; q < N; ++q)
-      if (q < L) kbuf[p + q] = k[q];
+      if (q < L) kbuf[p + q] = key_dec<K, kF>(k[q]);
   }
 }
 
@@ -318,7 +318,7 @@ __device__ __forceinline__ void pair_merge(T (&x)[16], bool upper) {
 //    the even lane holds items 0..15, the odd lane 16..31; after the network
 //    the lanes merge (pair_merge).  `pair` is warp-uniform.
 // Lanes without a segment (active = false) still take part in the shuffles.
-template <class K, bool kVals>
+template <class K, bool kVals, bool kF>
 __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, int L, bool active, bool pair,
                                       int lane) {
   const bool upper = pair && (lane & 1);
@@ -328,7 +328,8 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
     typename IO::T x[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-      x[q] = (active && base + q < L) ? IO::make(kbuf[p + base + q], base + q) : IO::sentinel(base + q);
+      x[q] = (active && base + q < L) ? IO::make(key_enc<K, kF>(kbuf[p + base + q]), base + q)
+                                      : IO::sentinel(base + q);
     Net<16>::run(x);
     if (pair) pair_merge(x, upper);
     uint32_t v[16];
@@ -339,7 +340,7 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       if (active && base + q < L) {
-        kbuf[p + base + q] = IO::key(x[q]);
+        kbuf[p + base + q] = key_dec<K, kF>(IO::key(x[q]));
         vbuf[pv + base + q] = v[q];
       }
     }
@@ -347,13 +348,13 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
     K x[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-      x[q] = (active && base + q < L) ? kbuf[p + base + q] : static_cast<K>(~static_cast<K>(0));
+      x[q] = (active && base + q < L) ? key_enc<K, kF>(kbuf[p + base + q]) : static_cast<K>(~static_cast<K>(0));
     Net<16>::run(x);
     if (pair) pair_merge(x, upper);
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-      if (active && base + q < L) kbuf[p + base + q] = x[q];
+      if (active && base + q < L) kbuf[p + base + q] = key_dec<K, kF>(x[q]);
   }
 }
 
@@ -396,14 +397,6 @@ __device__ __forceinline__ void bucket_network_class(int m, const RssMem<K>& rm,
     bucket_network<16, K, kVals>(rm, st, c);
 }
 
-// Comparator `c` of the step with XOR mask `mask` of the ascending bitonic
-// sorter (mask = k-1 for the mirrored first step of a merge of size k, else a
-// power of two): returns the lower slot; the partner is slot ^ mask.
-__device__ __forceinline__ int bitonic_slot(int c, int mask) {
-  const int h = (mask & (mask + 1)) == 0 ? (mask + 1) >> 1 : mask;  // highest bit of the pair distance
-  const int b = __ffs(h) - 1;
-  return ((c >> b) << (b + 1)) | (c & (h - 1));
-}
 
 // Warp-cooperative ascending bitonic sort of n <= 256 stored items at
 // rm[st..st+n), padded virtually to the next power of two with +inf:
@@ -453,7 +446,7 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K>& rm, int st, i
 //     (rare) are sorted by the whole warp (32-lane network, or a bitonic pass
 //     in shared memory above 32);
 //  7. write back (payload gathered by original position).
-template <class K, bool kVals>
+template <class K, bool kVals, bool kF>
 __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, const RssMem<K>& rm,
                                             int lane, int two_min) {
   using IO = ItemOf<K>;
@@ -465,11 +458,11 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
   It s0, s1;
   {
     const int q0 = ((2 * lane + 1) * L) / (2 * S);
-    s0 = IO::make(kbuf[p + q0], q0);
+    s0 = IO::make(key_enc<K, kF>(kbuf[p + q0]), q0);
     warp_network32(s0, lane);
     if (two) {
       const int q1 = ((2 * (32 + lane) + 1) * L) / (2 * S);
-      s1 = IO::make(kbuf[p + q1], q1);
+      s1 = IO::make(key_enc<K, kF>(kbuf[p + q1]), q1);
       warp_network32(s1, lane);
       // merge two ascending halves: slot l meets slot 63 - l; the smaller
       // items form a bitonic lower half, the larger a bitonic upper half
@@ -514,7 +507,7 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
   for (int r = 0; r < 8; ++r) {
     j[r] = 1;
     const int e = (r << 5) + lane;
-    x[r] = (r < rounds && e < L) ? IO::make(kbuf[p + e], e) : IO::sentinel(0);
+    x[r] = (r < rounds && e < L) ? IO::make(key_enc<K, kF>(kbuf[p + e]), e) : IO::sentinel(0);
   }
   // The top levels have few distinct nodes: they are broadcast once per
   // segment and picked with selects (nodes 1..7 for 8-byte items, 1..3 for
@@ -607,7 +600,7 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
       const int e = (r << 5) + lane;
       if (r < rounds && e < L) {
         const It y = rm.get(e);
-        kbuf[p + e] = IO::key(y);
+        kbuf[p + e] = key_dec<K, kF>(IO::key(y));
         vv[r] = vbuf[pv + IO::idx(y)];
       }
     }
@@ -621,7 +614,7 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int e = (r << 5) + lane;
-      if (r < rounds && e < L) kbuf[p + e] = IO::key(rm.get(e));
+      if (r < rounds && e < L) kbuf[p + e] = key_dec<K, kF>(IO::key(rm.get(e)));
     }
   }
   __syncwarp();
@@ -674,7 +667,7 @@ __device__ __forceinline__ TileTasks tile_tasks(const uint16_t* cnt) {
   return t;
 }
 
-template <class K, bool kVals, int kStages>
+template <class K, bool kVals, int kStages, bool kF>
 __global__ void __launch_bounds__(kTileThreads, 2)
     seg_tile_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
                     const Plan* plan, const uint32_t* __restrict__ tile_first, const uint16_t* __restrict__ counts,
@@ -948,16 +941,16 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       }
     }
     if (cls == 16) {
-      seg16<K, kVals>(kbuf, vbuf, p, pv, L, active, pair, lane);
+      seg16<K, kVals, kF>(kbuf, vbuf, p, pv, L, active, pair, lane);
     } else if (active) {
       if (cls == 12)
-        net_segment<12, K, kVals>(kbuf, vbuf, p, pv, L);
+        net_segment<12, K, kVals, kF>(kbuf, vbuf, p, pv, L);
       else if (cls == 8)
-        net_segment<8, K, kVals>(kbuf, vbuf, p, pv, L);
+        net_segment<8, K, kVals, kF>(kbuf, vbuf, p, pv, L);
       else if (cls == 4)
-        net_segment<4, K, kVals>(kbuf, vbuf, p, pv, L);
+        net_segment<4, K, kVals, kF>(kbuf, vbuf, p, pv, L);
       else
-        net_segment<2, K, kVals>(kbuf, vbuf, p, pv, L);
+        net_segment<2, K, kVals, kF>(kbuf, vbuf, p, pv, L);
     }
 
     // completion: the warp that finishes a tile's last item stores the tile
@@ -1020,7 +1013,7 @@ __device__ __forceinline__ void rss_issue(unsigned char* wbase, int b, uint64_t*
              static_cast<uint32_t>(vz - va), bar);
 }
 
-template <class K, bool kVals>
+template <class K, bool kVals, bool kF>
 __global__ void __launch_bounds__(kRssThreads, 2)
     seg_rss_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
                    const Plan* plan, const uint32_t* __restrict__ tile_first, const uint16_t* __restrict__ counts,
@@ -1061,7 +1054,7 @@ __global__ void __launch_bounds__(kRssThreads, 2)
     uint32_t* vbuf = reinterpret_cast<uint32_t*>(wbase + WL::kVals_ + b * WL::kValCap);
     const uint32_t ks = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(keys + pe0) & 15) / sizeof(K));
     const uint32_t vs = kVals ? static_cast<uint32_t>((reinterpret_cast<uintptr_t>(vals + pe0) & 15) / 4) : 0u;
-    rss_segment<K, kVals>(kbuf, vbuf, static_cast<int>(ks), static_cast<int>(vs), static_cast<int>(pL), rm, lane,
+    rss_segment<K, kVals, kF>(kbuf, vbuf, static_cast<int>(ks), static_cast<int>(vs), static_cast<int>(pL), rm, lane,
                           two_min);
     fence_proxy_async_smem();
     __syncwarp();
@@ -1163,7 +1156,7 @@ cudaError_t blocks_per_sm(Kern kern, int threads, int smem, int attr_smem, std::
   return cudaSuccess;
 }
 
-template <class K, bool kVals>
+template <class K, bool kVals, bool kF>
 cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, bool rss_only,
                        void* scratch, const SegTuning& tun, cudaStream_t stream, const DeviceInfo& d) {
   const uint32_t E = static_cast<uint32_t>(tun.tile_units);
@@ -1189,9 +1182,9 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
   {
     const TileLayout<K, kVals> lay(E);
     const int smem_bytes = static_cast<int>(lay.total(tun.tile_stages));
-    auto kern = tun.tile_stages == 2   ? seg_tile_kernel<K, kVals, 2>
-                : tun.tile_stages == 3 ? seg_tile_kernel<K, kVals, 3>
-                                       : seg_tile_kernel<K, kVals, 4>;
+    auto kern = tun.tile_stages == 2   ? seg_tile_kernel<K, kVals, 2, kF>
+                : tun.tile_stages == 3 ? seg_tile_kernel<K, kVals, 3, kF>
+                                       : seg_tile_kernel<K, kVals, 4, kF>;
     static std::atomic<int> cache[kCacheDevices * kCacheTileSizes * kMaxStages];
     int per_sm = 0;
     if ((e = blocks_per_sm(kern, kTileThreads, smem_bytes, static_cast<int>(kTileSmemLimit),
@@ -1206,7 +1199,7 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
   {
     using WL = RssWarpLayout<K, kVals>;
     const int smem_bytes = static_cast<int>(kRssWarps * WL::kBytes);
-    auto kern = seg_rss_kernel<K, kVals>;
+    auto kern = seg_rss_kernel<K, kVals, kF>;
     static std::atomic<int> cache[kCacheDevices * kCacheTileSizes * kMaxStages];
     int per_sm = 0;
     if ((e = blocks_per_sm(kern, kRssThreads, smem_bytes, smem_bytes, cache_slot(cache, d, 0, 2), &per_sm)) !=
@@ -1222,7 +1215,7 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
   return cudaSuccess;
 }
 
-template <class K>
+template <class K, bool kF = false>
 cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,
                             void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
                             const DeviceInfo& d) {
@@ -1232,8 +1225,8 @@ cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, ui
     return cudaErrorInvalidValue;
   if (scratch_bytes < ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total) return cudaErrorInvalidValue;
   const bool rss = mode == SegMode::kRssOnly;
-  return vals ? launch_all<K, true>(keys, vals, offsets, nseg, rss, scratch, t, s, d)
-              : launch_all<K, false>(keys, vals, offsets, nseg, rss, scratch, t, s, d);
+  return vals ? launch_all<K, true, kF>(keys, vals, offsets, nseg, rss, scratch, t, s, d)
+              : launch_all<K, false, kF>(keys, vals, offsets, nseg, rss, scratch, t, s, d);
 }
 
 }  // namespace

@@ -187,6 +187,55 @@ def batcher_odd_even(n: int):
     return pairs
 
 
+def bose_nelson(n: int):
+    """Bose and Nelson's recursive construction (1962), 0-based comparators in
+    the recursion's emission order (the order the paper calls locality-
+    optimised, BN-L): sort the first half and the second half, then merge
+    them with the recursive two-sequence merge."""
+    pairs = []
+
+    def merge(i: int, x: int, j: int, y: int) -> None:
+        # merge the sorted runs [i, i + x) and [j, j + y)
+        if x == 1 and y == 1:
+            pairs.append((i, j))
+        elif x == 1 and y == 2:
+            pairs.append((i, j + 1))
+            pairs.append((i, j))
+        elif x == 2 and y == 1:
+            pairs.append((i, j))
+            pairs.append((i + 1, j))
+        else:
+            a = x // 2
+            b = y // 2 if x % 2 else (y + 1) // 2
+            merge(i, a, j, b)
+            merge(i + a, x - a, j + b, y - b)
+            merge(i + a, x - a, j, b)
+
+    def sort(i: int, m: int) -> None:
+        if m > 1:
+            a = m // 2
+            sort(i, a)
+            sort(i + a, m - a)
+            merge(i, a, i + a, m - a)
+
+    sort(0, n)
+    return pairs
+
+
+def by_levels(net):
+    """The same comparators emitted level by level (as-soon-as-possible depth,
+    the order the paper calls parallelism-optimised, BN-P); stable within a
+    level."""
+    avail = {}
+    level_of = []
+    for a, b in net:
+        lv = max(avail.get(a, 0), avail.get(b, 0))
+        level_of.append(lv)
+        avail[a] = avail[b] = lv + 1
+    order = sorted(range(len(net)), key=lambda k: (level_of[k], k))
+    return [net[k] for k in order]
+
+
 def warp_schedule(width: int = 32):
     """XOR masks of the ascending bitonic sorter on ``width`` lanes."""
     masks = []
@@ -277,6 +326,15 @@ def render(chosen, masks) -> tuple[str, str]:
         lines.append(f"#define SN_NET_SIZE_{n} {len(net)}")
         lines.append(f"#define SN_NET_{n}(CE) {body}")
         lines.append("")
+    lines.append("/* Bose-Nelson networks (recursive construction, emission order of the")
+    lines.append(" * recursion): SN_BN_<n>(CE), same conventions as SN_NET_<n>. */")
+    for n in range(2, 17):
+        net = bose_nelson(n)
+        body = " ".join(f"CE({i},{j})" for i, j in net)
+        lines.append(f"/* n={n}: {len(net)} comparators, depth {depth(n, net)} */")
+        lines.append(f"#define SN_BN_SIZE_{n} {len(net)}")
+        lines.append(f"#define SN_BN_{n}(CE) {body}")
+    lines.append("")
     lines.append("/* 32-lane warp network (17..32 items): lane l exchanges with lane l ^ M at")
     lines.append(" * each step M below; the lower lane keeps the smaller item. */")
     lines.append(f"#define SN_WARP32_STEPS {len(masks)}")
@@ -291,6 +349,8 @@ def render(chosen, masks) -> tuple[str, str]:
                               "provenance": chosen[n]["provenance"]}
                      for n in range(2, 17)},
         "warp32": {"masks": masks, "pairs": [list(p) for p in schedule_pairs(masks)]},
+        "bose_nelson": {str(n): {"pairs": [list(p) for p in bose_nelson(n)], "size": len(bose_nelson(n)),
+                                 "depth": depth(n, bose_nelson(n))} for n in range(2, 17)},
     }
     return header, json.dumps(data, indent=1) + "\n"
 
@@ -300,6 +360,9 @@ def generate(check_only: bool = False) -> int:
     for n, rec in chosen.items():
         if not sorts_all_01(n, rec["pairs"]):
             raise RuntimeError(f"network for n={n} does not sort")
+    for n in range(2, 17):
+        if not sorts_all_01(n, bose_nelson(n)):
+            raise RuntimeError(f"Bose-Nelson network for n={n} does not sort")
     masks = warp_schedule(32)
     header, data = render(chosen, masks)
     if check_only:

@@ -105,3 +105,46 @@ def test_channel_removal_and_untangle():
     b8 = netgen.batcher_odd_even(8)
     assert len(b8) == 19 and oracle.network_depth(8, b8) == 6
     assert oracle.network_failures_perm(8, b8) == 0
+
+
+# ------------------------------------------------------------ Bose-Nelson --
+
+def test_bose_nelson_reproduces_the_printed_networks(golden_networks):
+    from paper_2002_05599_gb300.netgen import netgen as ng
+    for name, n in (("bnl16", 16), ("bn6", 6)):
+        gn, facts, levels = golden_networks[name]
+        printed = [p for lv in levels for p in lv]
+        gen = ng.bose_nelson(n)
+        assert gen == printed, name  # same comparators in the same order
+        assert len(gen) == facts["size"]
+    # the parallelism-ordered figure is the same network scheduled differently:
+    # every channel meets the same comparators in the same order
+    gn, facts, levels = golden_networks["bnp16"]
+    printed = [p for lv in levels for p in lv]
+    gen = ng.bose_nelson(16)
+
+    def per_channel(net):
+        return [[c for c in net if k in c] for k in range(16)]
+
+    assert per_channel(printed) == per_channel(gen) == per_channel(ng.by_levels(gen))
+    assert oracle.network_depth(16, gen) == oracle.network_depth(16, printed) == 15
+
+
+@pytest.mark.parametrize("n", range(2, 17))
+def test_bose_nelson_sorts_all_01_inputs(n):
+    from paper_2002_05599_gb300.netgen import netgen as ng
+    net = ng.bose_nelson(n)
+    assert oracle.network_failures_01(n, net) == 0
+    assert oracle.network_failures_01(n, ng.by_levels(net)) == 0
+    if n <= 8:
+        assert oracle.network_failures_perm(n, net) == 0
+
+
+def test_header_bose_nelson_tables_sort_and_match_the_generator():
+    from paper_2002_05599_gb300.netgen import netgen as ng
+    text = open(HEADER).read()
+    for n in range(2, 17):
+        m = re.search(rf"#define SN_BN_{n}\(CE\) (.*)", text)
+        pairs = [(int(a), int(b)) for a, b in re.findall(r"CE\((\d+),(\d+)\)", m.group(1))]
+        assert pairs == ng.bose_nelson(n)
+        assert oracle.network_failures_01(n, pairs) == 0

@@ -227,6 +227,98 @@ def test_rss_sorts(k, a):
 
 # --------------------------------------------------------------- mutation ----
 
+def _random_items(count, n, seed):
+    """Interleaved (key, ref) items with many equal keys; ref = input position."""
+    rng = np.random.default_rng(seed)
+    items = np.empty(2 * count * n, np.uint64)
+    items[0::2] = rng.integers(0, 5, count * n, dtype=np.uint64)
+    items[1::2] = np.arange(count * n, dtype=np.uint64)
+    return items
+
+
+def _items_reference(items, n):
+    """Each array ordered by (key, position in the array): Python's sort of index tuples."""
+    out = items.copy().reshape(-1, n, 2)
+    for a in range(out.shape[0]):
+        rows = [(int(out[a, i, 0]), i, int(out[a, i, 1])) for i in range(n)]
+        rows.sort()
+        for i, (k, _, r) in enumerate(rows):
+            out[a, i, 0], out[a, i, 1] = k, r
+    return out.reshape(-1)
+
+
+def test_items_sort_is_stable_by_key_with_references_attached():
+    for n in (2, 3, 8, 16):
+        items = _random_items(200, n, seed=n)
+        got = oracle.sort_fixed_items(items, n)
+        assert np.array_equal(got, _items_reference(items, n))
+        # keys alone agree with the keys-only oracle and numpy
+        keys = items[0::2].copy()
+        assert np.array_equal(got[0::2], oracle.sort_fixed(keys, n))
+        assert np.array_equal(got[0::2], np.sort(keys.reshape(-1, n), axis=1).reshape(-1))
+        # every (key, ref) pair survives
+        pairs_in = sorted(zip(items[0::2].tolist(), items[1::2].tolist()))
+        pairs_out = sorted(zip(got[0::2].tolist(), got[1::2].tolist()))
+        assert pairs_in == pairs_out
+
+
+def _f32(bits):
+    return np.array(bits, dtype=np.uint32).view(np.float32)
+
+
+def _total_order_key32(bits):
+    """IEEE 754 totalOrder of a binary32 bit pattern as a Python sort key, from
+    the standard's cases (NaN class by sign, numbers by value, -0 before +0,
+    NaNs of one sign by payload)."""
+    import math
+    bits = int(bits)
+    x = float(np.array([bits], np.uint32).view(np.float32)[0])  # numeric value (exact for non-NaN)
+    payload = bits & 0x7FFFFFFF
+    if (bits >> 23) & 0xFF == 0xFF and bits & 0x7FFFFF:  # NaN, read from the bits
+        return (0, -payload) if bits >> 31 else (2, payload)
+    zero_rank = 0 if math.copysign(1.0, x) < 0 else 1
+    return (1, x, zero_rank)
+
+
+def test_float_keys_follow_total_order_on_special_values():
+    expect = _f32([0xFFFFFFFF, 0xFFC00001, 0xFF800000, 0xFF7FFFFF, 0xBF800000, 0x80000001, 0x80000000,
+                   0x00000000, 0x00000001, 0x3F800000, 0x7F7FFFFF, 0x7F800000, 0x7F800001, 0x7FC00000,
+                   0x7FFFFFFF])
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        shuffled = rng.permutation(expect)
+        got = oracle.sort_fixed(shuffled, expect.size)
+        assert np.array_equal(got.view(np.uint32), expect.view(np.uint32))
+
+
+def test_float_keys_match_numpy_on_ordinary_values():
+    rng = np.random.default_rng(4)
+    for dt in (np.float32, np.float64):
+        keys = (rng.standard_normal(16 * 500) * 1e3).astype(dt)
+        keys[keys == 0] = 1  # no signed zeros: numpy treats -0 == +0
+        assert np.array_equal(oracle.sort_fixed(keys, 16), np.sort(keys.reshape(-1, 16), 1).reshape(-1))
+
+
+def test_float_keys_on_random_bit_patterns_against_python():
+    rng = np.random.default_rng(5)
+    bits = rng.integers(0, 2**32, 8 * 2000, dtype=np.uint64).astype(np.uint32)
+    bits[::7] = rng.choice([0x7FC00000, 0xFFC00000, 0x80000000, 0, 0x7F800000, 0xFF800000], bits[::7].size)
+    keys = bits.view(np.float32)
+    got = oracle.sort_fixed(keys, 8).view(np.uint32).reshape(-1, 8)
+    for a, row in enumerate(bits.reshape(-1, 8)):
+        order = sorted(range(8), key=lambda i: (_total_order_key32(row[i]), i))
+        assert np.array_equal(got[a], row[order])
+    # segments with payload: stable among equal bit patterns
+    k, v, off = wl.segment_batch(300, "geometric", "fewdistinct", np.uint32, True, seed=6)
+    kf = k.astype(np.float32) - np.float32(1.5)  # few distinct values, both signs
+    kb = kf.view(np.uint32)
+    gk, gv = oracle.sort_segments(kf, v, off)
+    for sgm in range(off.size - 1):
+        lo, hi = int(off[sgm]), int(off[sgm + 1])
+        order = sorted(range(lo, hi), key=lambda i: (_total_order_key32(kb[i]), i))
+        assert np.array_equal(gk[lo:hi], kf[order]) and np.array_equal(gv[lo:hi], v[order])
+
+
 _MUTATIONS = {
     # a wrong comparison sign in the fixed-size insertion sort
     "fixed_sign": ("while (j >= 0 && A[j] > x) {\n                A[j + 1] = A[j];\n                --j;\n            }\n            A[j + 1] = x;\n        }\n    }\n}\n\nvoid oracle_sort_fixed_u64",
@@ -244,6 +336,16 @@ _MUTATIONS = {
                   "for (int i = 0; i < n; ++i) x[i] = (int64_t)((v >> i) & 1u) * (i + 1 < n);"),
     # depth forgets the +1 per comparator
     "depth": ("        l += 1;\n", ""),
+    # unstable item sort (moves past equal keys)
+    "items_unstable": ("while (j >= 0 && A[2 * j] > key) {", "while (j >= 0 && A[2 * j] >= key) {"),
+    # the reference is not moved with its key
+    "items_ref": ("                A[2 * (j + 1) + 1] = A[2 * j + 1];\n", ""),
+    # -0 and +0 in the wrong order
+    "float_zero": ("return (signbit(a) == 0) && (signbit(b) != 0); /* +0 after -0 */",
+                   "return (signbit(a) != 0) && (signbit(b) == 0); /* +0 after -0 */"),
+    # negative NaNs ordered by payload the wrong way
+    "float_nan": ("    pa &= 0x7FFFFFFFu;\n    pb &= 0x7FFFFFFFu;\n    return ca > 0 ? pa > pb : pa < pb;",
+                  "    pa &= 0x7FFFFFFFu;\n    pb &= 0x7FFFFFFFu;\n    return pa > pb;"),
     # the permutation product drops a term
     "perm": ("    for (uint64_t i = 0; i < len; ++i) {\n        uint64_t ar = a[i] % p;",
              "    for (uint64_t i = 1; i < len; ++i) {\n        uint64_t ar = a[i] % p;"),
@@ -273,6 +375,15 @@ def _pins_pass(lib_path, golden):
             gk, gv = oracle.sort_segments(k, v, off)
             rk, rv = _stable_reference(k, v, off)
             ok &= np.array_equal(gk, rk) and np.array_equal(gv, rv)
+        special = _f32([0xFFC00000, 0xFFC00001, 0x80000000, 0, 0x7FC00001, 0x7FC00000, 0xBF800000])
+        ok &= np.array_equal(oracle.sort_fixed(special, 7).view(np.uint32),
+                             np.array([0xFFC00001, 0xFFC00000, 0xBF800000, 0x80000000, 0, 0x7FC00000,
+                                       0x7FC00001], np.uint32))
+        special64 = np.array([0x8000000000000000, 0, 0xBFF0000000000000, 0x7FF8000000000000], np.uint64)
+        ok &= np.array_equal(oracle.sort_fixed(special64[[1, 3, 0, 2]].view(np.float64), 4).view(np.uint64),
+                             special64[[2, 0, 1, 3]])
+        items = _random_items(40, 7, seed=9)
+        ok &= np.array_equal(oracle.sort_fixed_items(items, 7), _items_reference(items, 7))
         n, facts, levels = golden["opt10"]
         pairs = [p for lv in levels for p in lv]
         ok &= oracle.network_failures_01(n, pairs) == 0
