@@ -44,6 +44,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SWEEP_NS = list(range(2, 17))
+# DRAM bytes (read + write) of one full-size sweep step, from an ncu capture of the
+# fixed-n kernel at 2^22 arrays per n scaled to 2^24 (reads equal the algorithmic
+# reads; writes fall short by the output still resident in L2 at each kernel's end).
+SWEEP_DRAM_BYTES = 17_216_000_000
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "sorted Gkeys/s at 1 GB300 and % of HBM roofline"
 
@@ -348,7 +352,12 @@ def bench_ours(args, rank, world, local_rank, dist):
         "parts": parts_out,
         "roofline": {"bound": "hbm", "kernel": "fixed_tma_kernel (n=2..16, sweep)",
                      "achieved": round(sweep_gbs, 1), "peak": hbm, "peak_source": hbm_src,
-                     "unit": "GB/s", "frac": round(sweep_gbs / hbm, 4), "traffic": None},
+                     "unit": "GB/s", "frac": round(sweep_gbs / hbm, 4),
+                     "algorithmic_bytes": bytes_.get("sweep"),
+                     "traffic": SWEEP_DRAM_BYTES if (args.scale == 0 and "sweep" in parts) else None,
+                     "traffic_per": "one sweep step (15 launches, 2^24 arrays per n)",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at 2^22 arrays per n, "
+                                       "reads scaled x4, writes x4 less the ~65 MB per launch still in L2"},
         "gpu_launches": launches_per_step(parts) * args.steps,
         "clocks": clocks,
         "wall_s_timed_loop": round(wall, 3),
@@ -519,22 +528,29 @@ def bench_plain_vs_batched(args, sn, device, dist):
     off = wl.offsets_from_lengths(lens)
     total = int(off[-1])
     d_off = torch.from_numpy(off.view(np.int32)).to(device)
-    # plain layout: segments stably grouped by length (built once, untimed)
+    # plain layout: segments grouped by length, each length's block of arrays
+    # starting on a 16-byte boundary like a buffer of its own (built once, untimed)
+    counts = np.bincount(lens, minlength=17)
     order = np.argsort(lens, kind="stable")
     starts = off[:-1][order].astype(np.int64)
     glens = lens[order].astype(np.int64)
     gather = np.repeat(starts, glens) + (np.arange(total) - np.repeat(np.cumsum(glens) - glens, glens))
+    block_at, at = {}, 0
+    for n in range(1, 17):
+        at = (at + 3) & ~3  # 16 bytes for u32 keys, 32 for u64: aligned either way
+        block_at[n] = at
+        at += int(counts[n]) * n
+    place = np.concatenate([np.arange(block_at[n], block_at[n] + int(counts[n]) * n) for n in range(1, 17)])
     d_gather = torch.from_numpy(gather).to(device)
-    counts = np.bincount(lens, minlength=17)
+    d_place = torch.from_numpy(place).to(device)
+    padded = at
     for dtype, name, fixed, seg in ((np.uint64, "u64", sn.sn_sort_fixed_u64, sn.sn_sort_segments_u64),
                                     (np.uint32, "u32", sn.sn_sort_fixed, sn.sn_sort_segments)):
         keys = wl.uniform_keys_torch(total, dtype, seed=3, device=device)
-        grouped = keys[d_gather].contiguous()
+        grouped = torch.zeros(padded, dtype=keys.dtype, device=device)
+        grouped[d_place] = keys[d_gather]
         work_b, work_p = keys.clone(), grouped.clone()
-        views, at = {}, 0
-        for n in range(1, 17):
-            views[n] = work_p[at:at + counts[n] * n]
-            at += counts[n] * n
+        views = {n: work_p[block_at[n]:block_at[n] + int(counts[n]) * n] for n in range(1, 17)}
 
         def plain():
             for n in range(2, 17):
@@ -566,7 +582,7 @@ def bench_plain_vs_batched(args, sn, device, dist):
             res[label] = statistics.mean(times)
         sn.check(sn.sn_check(), "plain vs batched")
         # both forms sorted the same arrays: compare through the grouping
-        assert torch.equal(work_b[d_gather], work_p), "plain and batched results differ"
+        assert torch.equal(work_b[d_gather], work_p[d_place]), "plain and batched results differ"
         ms_p, ms_b = res["plain"], res["batched"]
         if dist:
             t = torch.tensor([ms_p, ms_b], dtype=torch.float64, device=device)
@@ -798,17 +814,19 @@ def oracle_step(sample):
     return keys, time.perf_counter() - t0
 
 
-def cpu_baseline(sizes, budget_s=12.0):
+def cpu_baseline(sizes, budget_s=15.0):
+    """The oracle on one host core, on the largest 2^-shift sample of the step
+    that a probe run predicts to take at most `budget_s` seconds."""
+    import math
     import oracle
     oracle.build()
-    shift = 10
+    shift = 9
+    sample, desc = oracle_sample(sizes, shift)
+    _, probe = oracle_step(sample)
+    grow = int(math.floor(math.log2(max(1.0, budget_s / max(probe, 1e-6)))))
+    shift = max(0, shift - grow)
     sample, desc = oracle_sample(sizes, shift)
     keys, sec = oracle_step(sample)
-    # grow the sample (halve the shift) while the run stays within the budget
-    while shift > 4 and sec * 2 < budget_s / 2:
-        shift -= 1
-        sample, desc = oracle_sample(sizes, shift)
-        keys, sec = oracle_step(sample)
     return {"value": round(keys / sec / 1e9, 5), "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
             "sample": desc, "seconds": round(sec, 3)}
 

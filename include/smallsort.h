@@ -231,6 +231,21 @@ int sn_sort_segments_large_u64(uint64_t *keys, uint32_t *vals, const uint32_t *o
                                sn_stream_t stream);
 
 /*
+ * One large array of n u32 keys sorted ascending, with this library's small
+ * sorters as the base case (library addition; the paper measures its sorters
+ * as base cases of Quicksort and IPS4o, Sec. 4.5 / 4.6).  One sample-sort
+ * partition splits the keys into buckets of about 128 (splitters from a
+ * sorted 4x oversample; keys classified as (key, position) pairs, so equal
+ * keys cannot pile up in one bucket); buckets of <= 256 keys are sorted by
+ * the segmented path, 257..4096 by the long-segment kernel, larger ones
+ * recursively.  Scratch: about 2n * 4 bytes plus small arrays from the
+ * library's pool (SN_ENOMEM if that fails).  The call synchronises `stream`
+ * (bucket counts are read back) and returns when the keys are sorted.
+ * n must be below 2^32 (SN_ERANGE); n <= 1 returns SN_OK.
+ */
+int sn_sort_large(uint32_t *keys, uint64_t n, sn_stream_t stream);
+
+/*
  * Synchronises `stream`, then returns and clears the device status word of the
  * current device: SN_ERANGE if a segmented call met bad offsets, SN_ETIMEOUT
  * if a bounded device wait ran out, SN_ECUDA if the stream reported a CUDA

@@ -14,6 +14,8 @@ Sets of Items".  What each function follows:
 * float32 / float64 keys (``sort_fixed``, ``sort_segments``) -- ordered by
   IEEE 754 totalOrder, written case by case from its definition (library
   addition: the paper's keys are integers).
+* ``sort_array``     -- one large u32 array, bottom-up merge sort (for the
+  large-array sort, where insertion sort would be too slow).
 * ``sort_fixed_items`` -- the same for the paper's 16-byte items (u64 key,
   u64 reference, Sec. 4.1), stable by key.
 * ``sort_segments``   -- per-segment stable insertion sort; payload values move
@@ -67,6 +69,8 @@ def _load():
     for name in ("oracle_sort_fixed_f32", "oracle_sort_fixed_f64"):
         getattr(lib, name).argtypes = [P, I, U64]
         getattr(lib, name).restype = None
+    lib.oracle_sort_array_u32.argtypes = [P, P, U64]
+    lib.oracle_sort_array_u32.restype = None
     lib.oracle_sort_fixed_items.argtypes = [P, I, U64]
     lib.oracle_sort_fixed_items.restype = None
     for name in ("oracle_sort_segments_u32", "oracle_sort_segments_u64", "oracle_sort_segments_f32",
@@ -105,6 +109,14 @@ def sort_fixed(keys: np.ndarray, n: int) -> np.ndarray:
           np.dtype(np.float32): lib.oracle_sort_fixed_f32,
           np.dtype(np.float64): lib.oracle_sort_fixed_f64}[out.dtype]
     fn(_ptr(out), n, out.size // n)
+    return out
+
+
+def sort_array(keys: np.ndarray) -> np.ndarray:
+    """A sorted copy of one u32 array (bottom-up merge sort)."""
+    out = np.ascontiguousarray(keys, dtype=np.uint32).copy()
+    tmp = np.empty_like(out)
+    _load().oracle_sort_array_u32(_ptr(out), _ptr(tmp), out.size)
     return out
 
 

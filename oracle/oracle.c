@@ -136,6 +136,32 @@ void oracle_sort_segments_u64(uint64_t *keys, uint32_t *vals,
     }
 }
 
+/*
+ * One array of n u32 keys sorted ascending by a bottom-up merge sort (runs of
+ * width 1, 2, 4, ... merged pairwise into a second buffer).  `tmp` holds n
+ * keys of scratch.  For the large-array sort, where insertion sort would take
+ * too long.
+ */
+void oracle_sort_array_u32(uint32_t *keys, uint32_t *tmp, uint64_t n)
+{
+    uint32_t *src = keys, *dst = tmp;
+    for (uint64_t w = 1; w < n; w *= 2) {
+        for (uint64_t lo = 0; lo < n; lo += 2 * w) {
+            uint64_t mid = lo + w < n ? lo + w : n;
+            uint64_t hi = lo + 2 * w < n ? lo + 2 * w : n;
+            uint64_t i = lo, j = mid, o = lo;
+            while (i < mid && j < hi) dst[o++] = (src[j] < src[i]) ? src[j++] : src[i++];
+            while (i < mid) dst[o++] = src[i++];
+            while (j < hi) dst[o++] = src[j++];
+        }
+        uint32_t *t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != keys)
+        for (uint64_t i = 0; i < n; ++i) keys[i] = src[i];
+}
+
 /* ---- Floating-point keys: IEEE 754 totalOrder ---- */
 
 /*

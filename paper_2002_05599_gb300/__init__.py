@@ -35,6 +35,7 @@ from ._binding import (  # noqa: F401
     sn_sort_fixed_family,
     sn_sort_fixed_items,
     sn_sort_fixed_u64,
+    sn_sort_large,
     sn_sort_segments,
     sn_sort_segments_f32,
     sn_sort_segments_f64,

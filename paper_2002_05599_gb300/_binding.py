@@ -155,6 +155,18 @@ def sn_sort_segments_f64(keys, vals, offsets, nseg: int | None = None, stream=No
 SN_MAX_SEGMENT_LARGE = 4096
 
 
+def sn_sort_large(keys, n: int | None = None, stream=None) -> int:
+    """Sort one array of u32 keys (sample-sort partition + segmented base case); synchronous."""
+    lib = library()
+    if not getattr(lib, "_large_bound", False):
+        lib.sn_sort_large.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+        lib.sn_sort_large.restype = ctypes.c_int
+        lib._large_bound = True
+    if n is None:
+        n = _elems(keys, 4)
+    return lib.sn_sort_large(_addr(keys), n, _stream(stream))
+
+
 def sn_sort_segments_large(keys, vals, offsets, nseg: int | None = None, stream=None) -> int:
     """Segments of up to SN_MAX_SEGMENT_LARGE u32 keys (one thread block per segment)."""
     return _segments(library().sn_sort_segments_large, 4, keys, vals, offsets, nseg, stream)

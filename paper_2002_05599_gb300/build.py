@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsmallsort.so")
 SOURCES = ["sn_api.cu", "sn_fixed_u32.cu", "sn_fixed_u64.cu", "sn_fixed_items.cu", "sn_fixed_float.cu",
-           "sn_segments_u32.cu", "sn_segments_u64.cu", "sn_segments_f32.cu", "sn_segments_f64.cu", "sn_large.cu", "sn_server.cu", "sn_tune.cu"]
+           "sn_segments_u32.cu", "sn_segments_u64.cu", "sn_segments_f32.cu", "sn_segments_f64.cu", "sn_large.cu", "sn_large_sort.cu", "sn_server.cu", "sn_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-I", INCLUDE, "-I", CSRC]

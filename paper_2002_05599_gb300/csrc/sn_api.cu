@@ -132,8 +132,8 @@ int segments_entry(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t ns
 
 template <class K>
 int large_entry(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream,
-                cudaError_t (*launch)(K*, uint32_t*, const uint32_t*, uint64_t, void*, cudaStream_t,
-                                      const sn::DeviceInfo&)) {
+                cudaError_t (*launch)(K*, uint32_t*, const uint32_t*, const uint32_t*, uint64_t, void*,
+                                      cudaStream_t, const sn::DeviceInfo&)) {
   if (nseg == 0) return SN_OK;
   if (keys == nullptr || offsets == nullptr) return SN_EINVAL;
   if (nseg >= (1ull << 32)) return SN_ERANGE;
@@ -156,7 +156,7 @@ int large_entry(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
     cudaGetLastError();
     return SN_ENOMEM;
   }
-  const cudaError_t e = launch(keys, vals, offsets, nseg, scratch, s, *d);
+  const cudaError_t e = launch(keys, vals, offsets, offsets + 1, nseg, scratch, s, *d);
   cudaFreeAsync(scratch, s);
   return e == cudaSuccess ? SN_OK : SN_ECUDA;
 }
@@ -226,6 +226,19 @@ int sn_sort_segments_large(uint32_t* keys, uint32_t* vals, const uint32_t* offse
 int sn_sort_segments_large_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
                                sn_stream_t stream) {
   return large_entry<uint64_t>(keys, vals, offsets, nseg, stream, sn::launch_large_u64);
+}
+
+int sn_sort_large(uint32_t* keys, uint64_t n, sn_stream_t stream) {
+  if (n <= 1) return SN_OK;
+  if (keys == nullptr) return SN_EINVAL;
+  if (n >= (1ull << 32)) return SN_ERANGE;
+  if (reinterpret_cast<uintptr_t>(keys) % 4 != 0) return SN_EINVAL;
+  int err = SN_OK;
+  const sn::DeviceInfo* d = sn::device_info(&err);
+  if (d == nullptr) return err;
+  const cudaError_t e = sn::sort_large_u32(keys, n, reinterpret_cast<cudaStream_t>(stream), *d);
+  if (e == cudaErrorMemoryAllocation) return SN_ENOMEM;
+  return e == cudaSuccess ? SN_OK : SN_ECUDA;
 }
 
 int rss_sort_segments(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, sn_stream_t stream) {

@@ -65,11 +65,16 @@ cudaError_t launch_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* 
                                 SegMode mode, void* scratch, size_t scratch_bytes, const SegTuning& t,
                                 cudaStream_t s, const DeviceInfo& d);
 // Segments of up to SN_MAX_SEGMENT_LARGE items, one CTA per segment
-// (sn_large.cu); `scratch` holds one device word (the validation flag).
-cudaError_t launch_large_u32(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, void* scratch,
-                             cudaStream_t s, const DeviceInfo& d);
-cudaError_t launch_large_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, void* scratch,
-                             cudaStream_t s, const DeviceInfo& d);
+// (sn_large.cu): segment s is keys[starts[s] .. ends[s]) (CSR offsets: ends =
+// offsets + 1); `scratch` holds one device word (the validation flag).
+cudaError_t launch_large_u32(uint32_t* keys, uint32_t* vals, const uint32_t* starts, const uint32_t* ends,
+                             uint64_t nseg, void* scratch, cudaStream_t s, const DeviceInfo& d);
+cudaError_t launch_large_u64(uint64_t* keys, uint32_t* vals, const uint32_t* starts, const uint32_t* ends,
+                             uint64_t nseg, void* scratch, cudaStream_t s, const DeviceInfo& d);
+
+// One large array of u32 keys, sample-sort partition + segmented base case
+// (sn_large_sort.cu); returns after the sort (it reads counts back).
+cudaError_t sort_large_u32(uint32_t* keys, uint64_t n, cudaStream_t s, const DeviceInfo& d);
 
 // f32 / f64 keys, ordered by IEEE-754 totalOrder (sn_segments_f32.cu / _f64.cu).
 cudaError_t launch_segments_f32(float* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,

@@ -22,12 +22,14 @@ namespace {
 constexpr int kLargeThreads = 256;
 constexpr uint32_t kLargeMax = SN_MAX_SEGMENT_LARGE;
 
+// Segment s is keys[starts[s] .. ends[s]); for CSR offsets, ends = offsets + 1.
 __global__ void __launch_bounds__(256)
-    large_check_kernel(const uint32_t* __restrict__ offsets, uint64_t nseg, unsigned* bad, unsigned* status) {
+    large_check_kernel(const uint32_t* __restrict__ starts, const uint32_t* __restrict__ ends, uint64_t nseg,
+                       unsigned* bad, unsigned* status) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   bool ok = true;
   for (uint64_t s = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < nseg; s += stride) {
-    const uint32_t a = offsets[s], b = offsets[s + 1];
+    const uint32_t a = starts[s], b = ends[s];
     if (b < a || b - a > kLargeMax) ok = false;
   }
   if (__any_sync(0xFFFFFFFFu, !ok) && (threadIdx.x & 31) == 0) {
@@ -66,8 +68,8 @@ constexpr size_t large_smem() {
 
 template <class K, bool kVals, bool kF>
 __global__ void __launch_bounds__(kLargeThreads)
-    large_sort_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
-                      uint64_t nseg, const unsigned* bad) {
+    large_sort_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ starts,
+                      const uint32_t* __restrict__ ends, uint64_t nseg, const unsigned* bad) {
   using IO = ItemOf<K>;
   extern __shared__ __align__(16) unsigned char smem[];
   if (*bad) return;
@@ -75,8 +77,8 @@ __global__ void __launch_bounds__(kLargeThreads)
   uint32_t* vs = reinterpret_cast<uint32_t*>(smem + LargeMem<K>::kItemBytes * kLargeMax);
   const int tid = threadIdx.x;
   for (uint64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
-    const uint32_t e0 = offsets[s];
-    const int L = static_cast<int>(offsets[s + 1] - e0);
+    const uint32_t e0 = starts[s];
+    const int L = static_cast<int>(ends[s] - e0);
     if (L <= 1) continue;
     int P = 2;
     while (P < L) P <<= 1;
@@ -114,14 +116,14 @@ __global__ void __launch_bounds__(kLargeThreads)
 }
 
 template <class K, bool kVals, bool kF>
-cudaError_t launch_large_t(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, void* scratch,
-                           cudaStream_t s, const DeviceInfo& d) {
+cudaError_t launch_large_t(K* keys, uint32_t* vals, const uint32_t* starts, const uint32_t* ends, uint64_t nseg,
+                           void* scratch, cudaStream_t s, const DeviceInfo& d) {
   unsigned* bad = static_cast<unsigned*>(scratch);
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   const unsigned g1 =
       static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>((nseg + 255) / 256, 8ull * d.sm_count)));
-  large_check_kernel<<<g1, 256, 0, s>>>(offsets, nseg, bad, d.status);
+  large_check_kernel<<<g1, 256, 0, s>>>(starts, ends, nseg, bad, d.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   constexpr int kSmem = static_cast<int>(large_smem<K, kVals>());
   static std::atomic<int> occ[64];
@@ -136,22 +138,22 @@ cudaError_t launch_large_t(K* keys, uint32_t* vals, const uint32_t* offsets, uin
   }
   const unsigned g2 = static_cast<unsigned>(
       std::max<uint64_t>(1, std::min<uint64_t>(nseg, static_cast<uint64_t>(d.sm_count) * per_sm)));
-  large_sort_kernel<K, kVals, kF><<<g2, kLargeThreads, kSmem, s>>>(keys, vals, offsets, nseg, bad);
+  large_sort_kernel<K, kVals, kF><<<g2, kLargeThreads, kSmem, s>>>(keys, vals, starts, ends, nseg, bad);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_large_u32(uint32_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, void* scratch,
-                             cudaStream_t s, const DeviceInfo& d) {
-  return vals ? launch_large_t<uint32_t, true, false>(keys, vals, offsets, nseg, scratch, s, d)
-              : launch_large_t<uint32_t, false, false>(keys, vals, offsets, nseg, scratch, s, d);
+cudaError_t launch_large_u32(uint32_t* keys, uint32_t* vals, const uint32_t* starts, const uint32_t* ends,
+                             uint64_t nseg, void* scratch, cudaStream_t s, const DeviceInfo& d) {
+  return vals ? launch_large_t<uint32_t, true, false>(keys, vals, starts, ends, nseg, scratch, s, d)
+              : launch_large_t<uint32_t, false, false>(keys, vals, starts, ends, nseg, scratch, s, d);
 }
 
-cudaError_t launch_large_u64(uint64_t* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, void* scratch,
-                             cudaStream_t s, const DeviceInfo& d) {
-  return vals ? launch_large_t<uint64_t, true, false>(keys, vals, offsets, nseg, scratch, s, d)
-              : launch_large_t<uint64_t, false, false>(keys, vals, offsets, nseg, scratch, s, d);
+cudaError_t launch_large_u64(uint64_t* keys, uint32_t* vals, const uint32_t* starts, const uint32_t* ends,
+                             uint64_t nseg, void* scratch, cudaStream_t s, const DeviceInfo& d) {
+  return vals ? launch_large_t<uint64_t, true, false>(keys, vals, starts, ends, nseg, scratch, s, d)
+              : launch_large_t<uint64_t, false, false>(keys, vals, starts, ends, nseg, scratch, s, d);
 }
 
 }  // namespace sn

@@ -247,6 +247,15 @@ def _items_reference(items, n):
     return out.reshape(-1)
 
 
+def test_array_merge_sort_matches_numpy_and_insertion_sort():
+    for n in (0, 1, 2, 3, 7, 64, 1000, 4097, 100_003):
+        keys = wl.uniform_keys(n, np.uint32, n + 1) % np.uint32(max(1, n // 3))
+        got = oracle.sort_array(keys)
+        assert np.array_equal(got, np.sort(keys))
+        if 0 < n <= 4097:  # the same result as the insertion-sort oracle on one array
+            assert np.array_equal(got, oracle.sort_fixed(keys, n))
+
+
 def test_items_sort_is_stable_by_key_with_references_attached():
     for n in (2, 3, 8, 16):
         items = _random_items(200, n, seed=n)
@@ -346,6 +355,8 @@ _MUTATIONS = {
     # negative NaNs ordered by payload the wrong way
     "float_nan": ("    pa &= 0x7FFFFFFFu;\n    pb &= 0x7FFFFFFFu;\n    return ca > 0 ? pa > pb : pa < pb;",
                   "    pa &= 0x7FFFFFFFu;\n    pb &= 0x7FFFFFFFu;\n    return pa > pb;"),
+    # the merge takes from the right run on ties and drops the last element of a run
+    "merge_drop": ("while (i < mid) dst[o++] = src[i++];", "while (i + 1 < mid) dst[o++] = src[i++];"),
     # the permutation product drops a term
     "perm": ("    for (uint64_t i = 0; i < len; ++i) {\n        uint64_t ar = a[i] % p;",
              "    for (uint64_t i = 1; i < len; ++i) {\n        uint64_t ar = a[i] % p;"),
@@ -384,6 +395,8 @@ def _pins_pass(lib_path, golden):
                              special64[[2, 0, 1, 3]])
         items = _random_items(40, 7, seed=9)
         ok &= np.array_equal(oracle.sort_fixed_items(items, 7), _items_reference(items, 7))
+        arr = wl.uniform_keys(3001, np.uint32, 9) % np.uint32(500)
+        ok &= np.array_equal(oracle.sort_array(arr), np.sort(arr))
         n, facts, levels = golden["opt10"]
         pairs = [p for lv in levels for p in lv]
         ok &= oracle.network_failures_01(n, pairs) == 0
