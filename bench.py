@@ -507,6 +507,41 @@ def bench_extras(args, sn, device):
         out.setdefault(f"large_{nseg}_segments_257..4096", {})[name] = {
             "ms": round(ms, 4), "gkeys_s": round(src.numel() / (ms * 1e-3) / 1e9, 1)}
         del src, work
+    # the rest of the RSS-range configuration: u64 keys, and Zipf(1.1) keys over 2^20 values
+    nseg = (1 << 20) >> args.scale
+    lens = wl.segment_lengths(nseg, "uniform", seed=101, lo=17, hi=256)
+    off = wl.offsets_from_lengths(lens)
+    d_off = torch.from_numpy(off.view(np.int32)).to(device)
+    total = int(off[-1])
+    variants = {}
+    for name, dt, fn, dist in (("u32_uniform", np.uint32, sn.rss_sort_segments, "uniform"),
+                               ("u32_zipf", np.uint32, sn.rss_sort_segments, "zipf"),
+                               ("u64_uniform", np.uint64, sn.rss_sort_segments_u64, "uniform"),
+                               ("u64_zipf", np.uint64, sn.rss_sort_segments_u64, "zipf")):
+        if dist == "uniform":
+            src = wl.uniform_keys_torch(total, dt, seed=101, device=device)
+        else:
+            src = wl.zipf_keys_torch(total, dtype=dt, seed=101, device=device)
+        work = src.clone()
+        ms = _time_calls(lambda: sn.check(fn(work, None, d_off)), lambda: work.copy_(src), reps, warm)
+        kb = np.dtype(dt).itemsize
+        variants[name] = {"ms": round(ms, 4), "gkeys_s": round(total / (ms * 1e-3) / 1e9, 2),
+                          "frac_hbm": round((2 * kb * total + 4 * (nseg + 1)) / (ms * 1e-3) / 1e9 / hbm, 4)}
+        del src, work
+    out[f"rss_range_{nseg}_segments_17..256_keys_only"] = variants
+
+    # one large array: sample-sort partition + segmented base case, next to torch.sort
+    n = (1 << 26) >> args.scale
+    src = wl.uniform_keys_torch(n, np.uint32, seed=703, device=device)
+    work = src.clone()
+    ms = _time_calls(lambda: sn.check(sn.sn_sort_large(work)), lambda: work.copy_(src), reps, warm)
+    ref = src.to(torch.int64) & 0xFFFFFFFF  # torch sorts signed values: widen so the u32 order is kept
+    ms_t = _time_calls(lambda: torch.sort(ref), lambda: None, reps, warm)
+    out[f"large_sort_2^{26 - args.scale}_u32"] = {
+        "sn_sort_large": {"ms": round(ms, 3), "gkeys_s": round(n / (ms * 1e-3) / 1e9, 2)},
+        "torch.sort (int64 view, library reference point)": {"ms": round(ms_t, 3),
+                                                             "gkeys_s": round(n / (ms_t * 1e-3) / 1e9, 2)}}
+    del src, work, ref
     sn.check(sn.sn_check(), "extras")
     return out
 

@@ -428,48 +428,51 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K>& rm, int st, i
 }
 
 // Register Sample Sort of one segment of L (17..256) items by one warp
-// (Sec. 3).  Items are (key, position-in-segment) pairs, all distinct.
+// (Sec. 3).  Splitters and classification use the keys alone; the buckets
+// then hold (key, position-in-segment) items and are sorted by both, so equal
+// keys end in input order.
 //
-//  1. sample: a*32 items at equidistant positions (a = 1, or 2 above
+//  1. sample: a*32 keys at equidistant positions (a = 1, or 2 above
 //     `two_min` items), sorted in registers by the 32-lane warp network
 //     (two halves merged for a = 2);
 //  2. splitters s_j = S_{j*a}, j = 1..31, as a heap-ordered tree held one node
 //     per lane (lane t holds node t) and broadcast by __shfl;
-//  3. classify: every item descends j <- 2j + [t_j < e] five times, so bucket
-//     b = j - 32 holds s_b < e <= s_{b+1}; its rank inside the bucket comes
-//     from a shared-memory counter (any order will do: each bucket is sorted
-//     afterwards);
+//  3. classify: every key descends j <- 2j + [t_j < e] five times, so bucket
+//     b = j - 32 holds s_b < e <= s_{b+1}; all keys equal to a splitter fall
+//     into one bucket; the rank inside the bucket comes from a shared-memory
+//     counter (any order will do: each bucket is sorted afterwards);
 //  4. bucket starts by a warp scan (lane b owns bucket b);
-//  5. scatter the items into the shared item buffer;
+//  5. scatter the (key, position) items into the shared item buffer;
 //  6. lane b sorts bucket b with a network padded to the warp's largest bucket
 //     of at most 16 items (4, 8, 12 or 16 channels); buckets above 16 items
-//     (rare) are sorted by the whole warp (32-lane network, or a bitonic pass
-//     in shared memory above 32);
+//     (rare unless keys repeat) are sorted by the whole warp (32-lane network,
+//     or a bitonic pass in shared memory above 32);
 //  7. write back (payload gathered by original position).
 template <class K, bool kVals, bool kF>
 __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, const RssMem<K>& rm,
                                             int lane, int two_min) {
   using IO = ItemOf<K>;
   using It = typename IO::T;
+  constexpr K kTop = static_cast<K>(~static_cast<K>(0));
 
-  // 1. sorted sample: slot q < 32 in s0 of lane q, slot 32 + q in s1 of lane q
+  // 1. sorted sample keys: slot q < 32 in s0 of lane q, slot 32 + q in s1 of lane q
   const bool two = L > two_min;
   const int S = two ? 64 : 32;
-  It s0, s1;
+  K s0, s1 = kTop;
   {
     const int q0 = ((2 * lane + 1) * L) / (2 * S);
-    s0 = IO::make(key_enc<K, kF>(kbuf[p + q0]), q0);
+    s0 = key_enc<K, kF>(kbuf[p + q0]);
     warp_network32(s0, lane);
     if (two) {
       const int q1 = ((2 * (32 + lane) + 1) * L) / (2 * S);
-      s1 = IO::make(key_enc<K, kF>(kbuf[p + q1]), q1);
+      s1 = key_enc<K, kF>(kbuf[p + q1]);
       warp_network32(s1, lane);
       // merge two ascending halves: slot l meets slot 63 - l; the smaller
-      // items form a bitonic lower half, the larger a bitonic upper half
+      // keys form a bitonic lower half, the larger a bitonic upper half
       // (in reversed lane order, still bitonic), each sorted by the
       // half-cleaners 16, 8, 4, 2, 1
-      const It y = shfl_idx(s1, 31 - lane);
-      It lo = pick(s0, y, true), hi = pick(s0, y, false);
+      const K y = shfl_idx(s1, 31 - lane);
+      K lo = pick(s0, y, true), hi = pick(s0, y, false);
 #pragma unroll
       for (int m = 16; m >= 1; m >>= 1) {
         const bool keep_min = lane < (lane ^ m);
@@ -483,38 +486,37 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
 
   // 2. tree node t (depth d, position p_d) = splitter (2 p_d + 1) * 2^(4 - d)
   //    = sample slot a * that - 1
-  It tree;
+  K tree;
   {
     const int t = lane > 0 ? lane : 1;
     const int d = 31 - __clz(t);
     const int rank = (2 * (t - (1 << d)) + 1) << (4 - d);
     const int slot = two ? 2 * rank - 1 : rank - 1;
-    const It from0 = shfl_idx(s0, slot & 31);
+    const K from0 = shfl_idx(s0, slot & 31);
     tree = from0;
     if (two) {
-      const It from1 = shfl_idx(s1, slot & 31);
+      const K from1 = shfl_idx(s1, slot & 31);
       tree = slot >= 32 ? from1 : from0;
     }
   }
   rm.cnt[lane] = 0;
   __syncwarp();
 
-  // 3. classify the register-resident items (item e = 32 r + lane)
+  // 3. classify the register-resident keys (item e = 32 r + lane)
   const int rounds = (L + 31) >> 5;
-  It x[8];
+  K xk[8];
   int j[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    j[r] = 1;
     const int e = (r << 5) + lane;
-    x[r] = (r < rounds && e < L) ? IO::make(key_enc<K, kF>(kbuf[p + e]), e) : IO::sentinel(0);
+    xk[r] = (r < rounds && e < L) ? key_enc<K, kF>(kbuf[p + e]) : kTop;
   }
   // The top levels have few distinct nodes: they are broadcast once per
-  // segment and picked with selects (nodes 1..7 for 8-byte items, 1..3 for
-  // the 12-byte items of u64 keys); the deeper levels read node j of lane j.
-  constexpr bool kNarrow = sizeof(It) == 8;
-  const It n1 = shfl_idx(tree, 1), n2 = shfl_idx(tree, 2), n3 = shfl_idx(tree, 3);
-  It n4 = n1, n5 = n1, n6 = n1, n7 = n1;
+  // segment and picked with selects (nodes 1..7 for 4-byte keys, 1..3 for
+  // 8-byte keys); the deeper levels read node j of lane j.
+  constexpr bool kNarrow = sizeof(K) == 4;
+  const K n1 = shfl_idx(tree, 1), n2 = shfl_idx(tree, 2), n3 = shfl_idx(tree, 3);
+  K n4 = n1, n5 = n1, n6 = n1, n7 = n1;
   if constexpr (kNarrow) {
     n4 = shfl_idx(tree, 4);
     n5 = shfl_idx(tree, 5);
@@ -523,9 +525,10 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
   }
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
+    j[r] = 1;
     if (r < rounds) {
-      j[r] = 2 + (item_less(n1, x[r]) ? 1 : 0);
-      j[r] = 2 * j[r] + (item_less(j[r] & 1 ? n3 : n2, x[r]) ? 1 : 0);
+      j[r] = 2 + (n1 < xk[r] ? 1 : 0);
+      j[r] = 2 * j[r] + ((j[r] & 1 ? n3 : n2) < xk[r] ? 1 : 0);
     }
   }
 #pragma unroll
@@ -533,12 +536,12 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       if (r < rounds) {
-        It t;
+        K t;
         if (kNarrow && lv == 2)
           t = j[r] & 2 ? (j[r] & 1 ? n7 : n6) : (j[r] & 1 ? n5 : n4);
         else
           t = shfl_idx(tree, j[r]);
-        j[r] = 2 * j[r] + (item_less(t, x[r]) ? 1 : 0);
+        j[r] = 2 * j[r] + (t < xk[r] ? 1 : 0);
       }
     }
   }
@@ -565,7 +568,8 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
   for (int r = 0; r < 8; ++r) {
     if (r < rounds) {
       const uint32_t st = __shfl_sync(kFull, start, (j[r] - 32) & 31);
-      if ((r << 5) + lane < L) rm.set(static_cast<int>(st + rank_in[r]), x[r]);
+      const int e = (r << 5) + lane;
+      if (e < L) rm.set(static_cast<int>(st + rank_in[r]), IO::make(xk[r], static_cast<uint32_t>(e)));
     }
   }
   __syncwarp();

@@ -178,3 +178,16 @@ def uniform_keys_torch(count: int, dtype, seed: int = 1, start: int = 0, device=
     if np.dtype(dtype) == np.uint32:
         return _lsr(bits, 32).to(torch.int32)
     return bits
+
+
+def zipf_keys_torch(count: int, s: float = 1.1, m: int = 1 << 20, dtype=np.uint32, seed: int = 1, device="cuda"):
+    """zipf_keys on a device (same values): the CDF is built on the host exactly
+    as zipf_keys does, the uniforms come from the same SplitMix64 stream, and
+    the inverse-CDF lookup is an exact binary search, so every key matches."""
+    import torch
+    ranks = np.arange(1, m + 1, dtype=np.float64)
+    cdf = torch.from_numpy(np.cumsum(ranks ** (-s))).to(device)
+    bits = splitmix64_torch(stream_seed(seed, TAG_ZIPF), 0, count, device)
+    u = (_lsr(bits, 11).to(torch.float64) + 1.0) * (1.0 / 9007199254740992.0) * cdf[-1]
+    r = torch.clamp(torch.searchsorted(cdf, u, side="left"), max=m - 1)
+    return r.to(torch.int32 if np.dtype(dtype) == np.uint32 else torch.int64)
