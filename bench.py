@@ -95,6 +95,33 @@ def config_dict(sizes, scale):
             "parallelism": "replicas (one independent batch per GPU)"}
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings over all ranks (identity without
+    a process group): the job's time is its slowest rank's."""
+    if not dist:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def sum_over_ranks(values, dist, device):
+    """Element-wise sum over all ranks (identity without a process group)."""
+    if not dist:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.tolist()
+
+
+def job_throughput(units_all_ranks, seconds):
+    """Whole-job throughput of weakly scaled replicas: the units every rank
+    processed, summed over the ranks, divided by the slowest rank's time."""
+    return units_all_ranks / seconds
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -312,10 +339,8 @@ def bench_ours(args, rank, world, local_rank, dist):
         per["rss"].append(c)
         per["step"].append(d)
     ms = {k: statistics.mean(v) for k, v in per.items()}
-    if dist:
-        t = torch.tensor([ms["step"], ms["sweep"], ms["uneven"], ms["rss"]], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = dict(zip(["step", "sweep", "uneven", "rss"], t.tolist()))
+    ms = dict(zip(["step", "sweep", "uneven", "rss"],
+                  max_over_ranks([ms["step"], ms["sweep"], ms["uneven"], ms["rss"]], dist, device)))
 
     hbm, hbm_src = peaks()
     sweep_gbs = bytes_["sweep"] / (ms["sweep"] * 1e-3) / 1e9 if "sweep" in parts else 0.0
@@ -334,10 +359,11 @@ def bench_ours(args, rank, world, local_rank, dist):
         parts_out[p] = {"ms": round(ms[p], 4), "gkeys_s": round(keys[p] / (ms[p] * 1e-3) / 1e9, 2),
                         "gb_s": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4), "keys": keys[p], "bytes": bytes_[p]}
     total_keys = sum(keys[p] for p in parts)
+    job_keys = sum_over_ranks([total_keys], dist, device)[0]  # ranks draw their own segment lengths
 
     result = {
         "metric": METRIC,
-        "value": round(world * total_keys / (ms["step"] * 1e-3) / 1e9, 3),
+        "value": round(job_throughput(job_keys, ms["step"] * 1e-3) / 1e9, 3),
         "unit": "Gkeys/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -619,10 +645,7 @@ def bench_plain_vs_batched(args, sn, device, dist):
         # both forms sorted the same arrays: compare through the grouping
         assert torch.equal(work_b[d_gather], work_p[d_place]), "plain and batched results differ"
         ms_p, ms_b = res["plain"], res["batched"]
-        if dist:
-            t = torch.tensor([ms_p, ms_b], dtype=torch.float64, device=device)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_p, ms_b = t.tolist()
+        ms_p, ms_b = max_over_ranks([ms_p, ms_b], dist, device)
         out[name] = {"plain_ms": round(ms_p, 4), "plain_gkeys_s": round(total / (ms_p * 1e-3) / 1e9, 2),
                      "plain_launches": int(sum(1 for n in range(2, 17) if counts[n])),
                      "batched_ms": round(ms_b, 4), "batched_gkeys_s": round(total / (ms_b * 1e-3) / 1e9, 2),
@@ -804,12 +827,10 @@ def bench_e2e(args, sn, pristine, world, dist, device, parts=PARTS):
         step()
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / steps
-    if dist:
-        t = torch.tensor([sec], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
+    sec = max_over_ranks([sec], dist, device)[0]
+    job_keys = sum_over_ranks([keys], dist, device)[0]
     sn.check(sn.sn_check(), "e2e")
-    return {"value": round(world * keys / sec / 1e9, 3), "unit": "Gkeys/s", "ms_per_step": round(sec * 1e3, 3),
+    return {"value": round(job_throughput(job_keys, sec) / 1e9, 3), "unit": "Gkeys/s", "ms_per_step": round(sec * 1e3, 3),
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
             "pipeline": f"{len(jobs)} jobs; H2D, sorts and D2H on three streams"}
 
