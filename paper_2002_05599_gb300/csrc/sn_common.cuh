@@ -57,6 +57,7 @@ template <> struct ItemOf<uint64_t> {
   }
 };
 
+__device__ __forceinline__ bool item_less(uint32_t a, uint32_t b) { return a < b; }
 __device__ __forceinline__ bool item_less(uint64_t a, uint64_t b) { return a < b; }
 __device__ __forceinline__ bool item_less(const Item64& a, const Item64& b) {
   return a.key < b.key || (a.key == b.key && a.idx < b.idx);

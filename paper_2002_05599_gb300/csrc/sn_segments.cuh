@@ -41,6 +41,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "sn_common.cuh"
 #include "sn_internal.h"
@@ -109,12 +110,31 @@ struct TileLayout {
   }
 };
 
-// Per-warp Register Sample Sort scratch: 256 items + 64 bucket counters.  The
-// item buffer also holds the sorted sample (slots 0..S-1) and the splitter
-// tree (slots S..S+k-1) until the scatter overwrites it, which happens only
-// after every item is classified.
-template <class K> struct RssMem;
-template <> struct RssMem<uint32_t> {
+// Items of the RSS buckets: (key, position) pairs when a payload must follow
+// its key, bare keys otherwise (equal keys are then interchangeable).
+template <class K>
+struct KeyOnly {
+  using T = K;
+  static __device__ __forceinline__ K make(K key, uint32_t) { return key; }
+  static __device__ __forceinline__ K key(K it) { return it; }
+  static __device__ __forceinline__ uint32_t idx(K) { return 0; }
+  static __device__ __forceinline__ K sentinel(uint32_t) { return static_cast<K>(~static_cast<K>(0)); }
+};
+template <class K, bool kVals>
+using RssIO = typename std::conditional<kVals, ItemOf<K>, KeyOnly<K>>::type;
+
+// Per-warp Register Sample Sort scratch: 256 bucket items + 32 bucket counters.
+template <class K, bool kVals> struct RssMem;
+template <class K> struct RssMem<K, false> {
+  static constexpr size_t kBytes = 256 * sizeof(K) + kRssMaxBuckets * 4;
+  K* key;
+  uint32_t* cnt;
+  __device__ __forceinline__ explicit RssMem(unsigned char* p)
+      : key(reinterpret_cast<K*>(p)), cnt(reinterpret_cast<uint32_t*>(p + 256 * sizeof(K))) {}
+  __device__ __forceinline__ K get(int i) const { return key[i]; }
+  __device__ __forceinline__ void set(int i, K v) const { key[i] = v; }
+};
+template <> struct RssMem<uint32_t, true> {
   static constexpr size_t kBytes = 256 * 8 + kRssMaxBuckets * 4;
   uint64_t* buf;  // packed (key, position) items
   uint32_t* cnt;
@@ -123,7 +143,7 @@ template <> struct RssMem<uint32_t> {
   __device__ __forceinline__ uint64_t get(int i) const { return buf[i]; }
   __device__ __forceinline__ void set(int i, uint64_t v) const { buf[i] = v; }
 };
-template <> struct RssMem<uint64_t> {
+template <> struct RssMem<uint64_t, true> {
   static constexpr size_t kBytes = 256 * 8 + 256 * 2 + kRssMaxBuckets * 4;
   uint64_t* key;
   uint16_t* idx;
@@ -148,7 +168,7 @@ struct RssWarpLayout {
   static constexpr size_t kKeys = 16;
   static constexpr size_t kVals_ = kKeys + 2 * kKeyCap;
   static constexpr size_t kScratch = (kVals_ + 2 * kValCap + 15) & ~static_cast<size_t>(15);
-  static constexpr size_t kBytes = (kScratch + RssMem<K>::kBytes + 127) & ~static_cast<size_t>(127);
+  static constexpr size_t kBytes = (kScratch + RssMem<K, kVals>::kBytes + 127) & ~static_cast<size_t>(127);
 };
 
 // ---------------------------------------------------------------- plan -----
@@ -362,8 +382,8 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
 
 // Bucket of c (<= N) items at rm[st..st+c), padded to N with +inf.
 template <int N, class K, bool kVals>
-__device__ __forceinline__ void bucket_network(const RssMem<K>& rm, int st, int c) {
-  using IO = ItemOf<K>;
+__device__ __forceinline__ void bucket_network(const RssMem<K, kVals>& rm, int st, int c) {
+  using IO = RssIO<K, kVals>;
   if constexpr (kVals) {
     typename IO::T it[N];
 #pragma unroll
@@ -373,20 +393,19 @@ __device__ __forceinline__ void bucket_network(const RssMem<K>& rm, int st, int 
     for (int q = 0; q < N; ++q)
       if (q < c) rm.set(st + q, it[q]);
   } else {
-    // keys only: equal keys are interchangeable, so the network orders keys
-    // alone (the stored position is not needed after classification)
+    // keys only: equal keys are interchangeable
     K k[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) k[q] = q < c ? IO::key(rm.get(st + q)) : static_cast<K>(~static_cast<K>(0));
+    for (int q = 0; q < N; ++q) k[q] = q < c ? rm.get(st + q) : static_cast<K>(~static_cast<K>(0));
     Net<N>::run(k);
 #pragma unroll
     for (int q = 0; q < N; ++q)
-      if (q < c) rm.set(st + q, IO::make(k[q], 0));
+      if (q < c) rm.set(st + q, k[q]);
   }
 }
 
 template <class K, bool kVals>
-__device__ __forceinline__ void bucket_network_class(int m, const RssMem<K>& rm, int st, int c) {
+__device__ __forceinline__ void bucket_network_class(int m, const RssMem<K, kVals>& rm, int st, int c) {
   if (m <= 4)
     bucket_network<4, K, kVals>(rm, st, c);
   else if (m <= 8)
@@ -401,9 +420,8 @@ __device__ __forceinline__ void bucket_network_class(int m, const RssMem<K>& rm,
 // Warp-cooperative ascending bitonic sort of n <= 256 stored items at
 // rm[st..st+n), padded virtually to the next power of two with +inf:
 // comparators that reach past n are skipped.
-template <class K, bool kByKey>
-__device__ __forceinline__ void warp_bitonic_smem(const RssMem<K>& rm, int st, int n, int lane) {
-  using IO = ItemOf<K>;
+template <class K, bool kVals>
+__device__ __forceinline__ void warp_bitonic_smem(const RssMem<K, kVals>& rm, int st, int n, int lane) {
   int P = 1;
   while (P < n) P <<= 1;
   for (int k = 2; k <= P; k <<= 1) {
@@ -414,8 +432,7 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K>& rm, int st, i
         if (j < n) {
           const auto a = rm.get(st + i);
           const auto b = rm.get(st + j);
-          const bool swap = kByKey ? (IO::key(b) < IO::key(a)) : item_less(b, a);
-          if (swap) {
+          if (item_less(b, a)) {
             rm.set(st + i, b);
             rm.set(st + j, a);
           }
@@ -449,9 +466,9 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K>& rm, int st, i
 //     or a bitonic pass in shared memory above 32);
 //  7. write back (payload gathered by original position).
 template <class K, bool kVals, bool kF>
-__device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L, const RssMem<K>& rm,
-                                            int lane, int two_min) {
-  using IO = ItemOf<K>;
+__device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L,
+                                            const RssMem<K, kVals>& rm, int lane, int two_min) {
+  using IO = RssIO<K, kVals>;
   using It = typename IO::T;
   constexpr K kTop = static_cast<K>(~static_cast<K>(0));
 
@@ -591,7 +608,7 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
       __syncwarp();
       if (lane < cb) rm.set(st + lane, y);
     } else {
-      warp_bitonic_smem<K, !kVals>(rm, st, cb, lane);
+      warp_bitonic_smem<K, kVals>(rm, st, cb, lane);
     }
     __syncwarp();
   }
@@ -1028,7 +1045,7 @@ __global__ void __launch_bounds__(kRssThreads, 2)
   const int lane = threadIdx.x & 31;
   unsigned char* wbase = smem + warp * WL::kBytes;
   uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + WL::kBar);
-  const RssMem<K> rm(wbase + WL::kScratch);
+  const RssMem<K, kVals> rm(wbase + WL::kScratch);
   if (lane == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
