@@ -83,6 +83,32 @@ __device__ __forceinline__ void ce(Item64& a, Item64& b) {
   b = hi;
 }
 
+// A key with its position, ordered by the key alone: the first network pass of
+// the payload paths.  Equal keys may end out of position order; a check of
+// adjacent items finds that, and a (key, position) pass then fixes it.
+template <class K>
+struct KeyIdx {
+  K k;
+  uint32_t ix;
+};
+template <class K>
+__device__ __forceinline__ bool item_less(const KeyIdx<K>& a, const KeyIdx<K>& b) {
+  return a.k < b.k;
+}
+template <class K>
+__device__ __forceinline__ void ce(KeyIdx<K>& a, KeyIdx<K>& b) {
+  const bool swap = b.k < a.k;
+  const KeyIdx<K> lo{swap ? b.k : a.k, swap ? b.ix : a.ix};
+  const KeyIdx<K> hi{swap ? a.k : b.k, swap ? a.ix : b.ix};
+  a = lo;
+  b = hi;
+}
+// Adjacent items with equal keys out of position order.
+template <class K>
+__device__ __forceinline__ bool tie_misordered(const KeyIdx<K>& a, const KeyIdx<K>& b) {
+  return a.k == b.k && a.ix > b.ix;
+}
+
 // Min/max of two items for the warp network: `keep_min` selects the result.
 __device__ __forceinline__ uint32_t pick(uint32_t mine, uint32_t other, bool keep_min) {
   return keep_min ? min(mine, other) : max(mine, other);
@@ -91,8 +117,9 @@ __device__ __forceinline__ uint64_t pick(uint64_t mine, uint64_t other, bool kee
   return keep_min ? min(mine, other) : max(mine, other);
 }
 __device__ __forceinline__ Item64 pick(const Item64& mine, const Item64& other, bool keep_min) {
-  const bool other_smaller = item_less(other, mine);
-  return (other_smaller == keep_min) ? other : mine;
+  // the partner's item only if strictly on the wanted side (equal items: keep mine)
+  const bool take = keep_min ? item_less(other, mine) : item_less(mine, other);
+  return take ? other : mine;
 }
 
 // -------------------------------------------------------- networks --------
@@ -185,6 +212,10 @@ __device__ __forceinline__ uint32_t shfl_xor(uint32_t v, int m) { return __shfl_
 __device__ __forceinline__ uint64_t shfl_xor(uint64_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
 __device__ __forceinline__ Item64 shfl_xor(const Item64& v, int m) {
   return Item64{__shfl_xor_sync(0xFFFFFFFFu, v.key, m), __shfl_xor_sync(0xFFFFFFFFu, v.idx, m)};
+}
+template <class K>
+__device__ __forceinline__ KeyIdx<K> shfl_xor(const KeyIdx<K>& v, int m) {
+  return KeyIdx<K>{shfl_xor(v.k, m), __shfl_xor_sync(0xFFFFFFFFu, v.ix, m)};
 }
 
 __device__ __forceinline__ uint32_t shfl_idx(uint32_t v, int src) { return __shfl_sync(0xFFFFFFFFu, v, src); }

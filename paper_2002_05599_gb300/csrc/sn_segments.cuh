@@ -262,19 +262,34 @@ __global__ void __launch_bounds__(256)
 template <int N, class K, bool kVals, bool kF>
 __device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L) {
   if constexpr (kVals) {
-    using IO = ItemOf<K>;
-    typename IO::T it[N];
+    // network on keys with positions carried; equal keys left out of position
+    // order (rare) are fixed by a second, (key, position) pass
+    KeyIdx<K> it[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) it[q] = q < L ? IO::make(key_enc<K, kF>(kbuf[p + q]), q) : IO::sentinel(q);
+    for (int q = 0; q < N; ++q)
+      it[q] = KeyIdx<K>{q < L ? key_enc<K, kF>(kbuf[p + q]) : static_cast<K>(~static_cast<K>(0)),
+                        static_cast<uint32_t>(q)};
     Net<N>::run(it);
+    bool tie = false;
+#pragma unroll
+    for (int q = 0; q + 1 < N; ++q) tie |= tie_misordered(it[q], it[q + 1]);
+    if (tie) {
+      using IO = ItemOf<K>;
+      typename IO::T full[N];
+#pragma unroll
+      for (int q = 0; q < N; ++q) full[q] = IO::make(it[q].k, it[q].ix);
+      Net<N>::run(full);
+#pragma unroll
+      for (int q = 0; q < N; ++q) it[q] = KeyIdx<K>{IO::key(full[q]), IO::idx(full[q])};
+    }
     uint32_t v[N];
 #pragma unroll
     for (int q = 0; q < N; ++q)
-      if (q < L) v[q] = vbuf[pv + IO::idx(it[q])];
+      if (q < L) v[q] = vbuf[pv + it[q].ix];
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       if (q < L) {
-        kbuf[p + q] = key_dec<K, kF>(IO::key(it[q]));
+        kbuf[p + q] = key_dec<K, kF>(it[q].k);
         vbuf[pv + q] = v[q];
       }
     }
@@ -291,13 +306,15 @@ __device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int 
 
 // ---------------------------------------------------- 17..32 on two lanes --
 
+// The smaller / larger of the lane's item `a` and its partner's `b`; on equal
+// keys each lane keeps its own item, so the exchange stays a permutation.
 template <class T>
 __device__ __forceinline__ T lo_of(const T& a, const T& b) {
   return item_less(b, a) ? b : a;
 }
 template <class T>
 __device__ __forceinline__ T hi_of(const T& a, const T& b) {
-  return item_less(b, a) ? a : b;
+  return item_less(a, b) ? b : a;
 }
 __device__ __forceinline__ uint32_t lo_of(uint32_t a, uint32_t b) { return min(a, b); }
 __device__ __forceinline__ uint32_t hi_of(uint32_t a, uint32_t b) { return max(a, b); }
@@ -344,23 +361,43 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
   const bool upper = pair && (lane & 1);
   const int base = upper ? 16 : 0;
   if constexpr (kVals) {
-    using IO = ItemOf<K>;
-    typename IO::T x[16];
+    // network (and pair merge) on keys with positions carried; if equal keys
+    // were left out of position order anywhere in the warp (rare), every lane
+    // repeats the work on (key, position) items
+    KeyIdx<K> x[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-      x[q] = (active && base + q < L) ? IO::make(key_enc<K, kF>(kbuf[p + base + q]), base + q)
-                                      : IO::sentinel(base + q);
+      x[q] = KeyIdx<K>{(active && base + q < L) ? key_enc<K, kF>(kbuf[p + base + q])
+                                                : static_cast<K>(~static_cast<K>(0)),
+                       static_cast<uint32_t>(base + q)};
     Net<16>::run(x);
     if (pair) pair_merge(x, upper);
+    bool tie = false;
+#pragma unroll
+    for (int q = 0; q < 15; ++q) tie |= tie_misordered(x[q], x[q + 1]);
+    if (pair) {  // the boundary between the even lane's last item and the odd lane's first
+      const KeyIdx<K> prev = shfl_xor(x[15], 1);
+      if (upper) tie |= tie_misordered(prev, x[0]);
+    }
+    if (__any_sync(kFull, tie)) {
+      using IO = ItemOf<K>;
+      typename IO::T full[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) full[q] = IO::make(x[q].k, x[q].ix);
+      Net<16>::run(full);
+      if (pair) pair_merge(full, upper);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) x[q] = KeyIdx<K>{IO::key(full[q]), IO::idx(full[q])};
+    }
     uint32_t v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-      if (active && base + q < L) v[q] = vbuf[pv + IO::idx(x[q])];
+      if (active && base + q < L) v[q] = vbuf[pv + x[q].ix];
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       if (active && base + q < L) {
-        kbuf[p + base + q] = key_dec<K, kF>(IO::key(x[q]));
+        kbuf[p + base + q] = key_dec<K, kF>(x[q].k);
         vbuf[pv + base + q] = v[q];
       }
     }
@@ -540,19 +577,20 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
     n6 = shfl_idx(tree, 6);
     n7 = shfl_idx(tree, 7);
   }
+  // The descent has no branch inside: it runs over 4 or all 8 rounds (keys
+  // past the segment are +inf, sink to the last bucket and are never
+  // counted), so the independent rounds interleave.
+  auto descend = [&](auto R_) {
+    constexpr int R = decltype(R_)::value;
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    j[r] = 1;
-    if (r < rounds) {
+    for (int r = 0; r < R; ++r) {
       j[r] = 2 + (n1 < xk[r] ? 1 : 0);
       j[r] = 2 * j[r] + ((j[r] & 1 ? n3 : n2) < xk[r] ? 1 : 0);
     }
-  }
 #pragma unroll
-  for (int lv = 2; lv < 5; ++lv) {
+    for (int lv = 2; lv < 5; ++lv) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      if (r < rounds) {
+      for (int r = 0; r < R; ++r) {
         K t;
         if (kNarrow && lv == 2)
           t = j[r] & 2 ? (j[r] & 1 ? n7 : n6) : (j[r] & 1 ? n5 : n4);
@@ -561,7 +599,13 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
         j[r] = 2 * j[r] + (t < xk[r] ? 1 : 0);
       }
     }
-  }
+  };
+#pragma unroll
+  for (int r = 0; r < 8; ++r) j[r] = 32;
+  if (rounds <= 4)
+    descend(std::integral_constant<int, 4>{});
+  else
+    descend(std::integral_constant<int, 8>{});
   uint32_t rank_in[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
