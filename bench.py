@@ -626,8 +626,14 @@ def bench_plain_vs_batched(args, sn, device, dist):
             work_b.copy_(keys)
             tuning = autotune(sn, work_b, None, d_off)
 
+        def plain_from_csr():  # what a caller holding the CSR batch has to do for the plain form
+            work_p[d_place] = work_b[d_gather]
+            plain()
+            work_b[d_gather] = work_p[d_place]
+
         res = {}
-        for label, fn, src, dst in (("plain", plain, grouped, work_p), ("batched", batched, keys, work_b)):
+        for label, fn, src, dst in (("plain", plain, grouped, work_p), ("batched", batched, keys, work_b),
+                                    ("plain_from_csr", plain_from_csr, keys, work_b)):
             for _ in range(max(3, args.warmup)):
                 dst.copy_(src)
                 fn()
@@ -642,14 +648,22 @@ def bench_plain_vs_batched(args, sn, device, dist):
                 times.append(a.elapsed_time(b))
             res[label] = statistics.mean(times)
         sn.check(sn.sn_check(), "plain vs batched")
-        # both forms sorted the same arrays: compare through the grouping
+        # both forms sort the same arrays: compare through the grouping
+        work_b.copy_(keys)
+        batched()
+        work_p.copy_(grouped)
+        plain()
         assert torch.equal(work_b[d_gather], work_p[d_place]), "plain and batched results differ"
-        ms_p, ms_b = res["plain"], res["batched"]
-        ms_p, ms_b = max_over_ranks([ms_p, ms_b], dist, device)
+        ms_p, ms_b, ms_c = max_over_ranks([res["plain"], res["batched"], res["plain_from_csr"]], dist, device)
         out[name] = {"plain_ms": round(ms_p, 4), "plain_gkeys_s": round(total / (ms_p * 1e-3) / 1e9, 2),
                      "plain_launches": int(sum(1 for n in range(2, 17) if counts[n])),
                      "batched_ms": round(ms_b, 4), "batched_gkeys_s": round(total / (ms_b * 1e-3) / 1e9, 2),
                      "batched_launches": 4, "batched_over_plain": round(ms_p / ms_b, 3),
+                     "plain_from_csr_ms": round(ms_c, 4),
+                     "plain_from_csr_gkeys_s": round(total / (ms_c * 1e-3) / 1e9, 2),
+                     "plain_from_csr_note": "group the CSR batch by length (gather), one launch per n, "
+                                            "scatter back (torch indexing for the data movement)",
+                     "batched_over_plain_from_csr": round(ms_c / ms_b, 3),
                      "batched_launch_parameters": tuning}
         del keys, grouped, work_b, work_p, views
     return out

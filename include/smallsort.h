@@ -183,6 +183,8 @@ typedef struct {
                               shorter ones 32 (16..256, default 160) */
     int tile_stages;       /* staging depth of the network kernel: 2..4 tiles in flight per block
                               (default 2); tile_stages x tile size must fit in shared memory */
+    int tile_mode;         /* network kernel: 0 = warps take work items from a task ring (default),
+                              1 = all warps of a block work through each staged tile together */
 } sn_tuning;
 
 /* Current parameters of the current device for (key_bytes = 4 or 8, with_vals = 0 or 1). */
@@ -194,8 +196,8 @@ int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning *t);
 /*
  * Autotuner: times sn_sort_segments on the caller's batch (device pointers,
  * same contract as sn_sort_segments / _u64 with key_bytes 4 / 8) under
- * candidate parameters -- a coordinate search over net_classes, (tile_units,
- * tile_stages) and rss_two_min, best of three runs each, the input restored from a device
+ * candidate parameters -- a coordinate search over tile_mode, net_classes,
+ * (tile_units, tile_stages) and rss_two_min, best of three runs each, the input restored from a device
  * copy before every run -- installs the fastest set for this key type and
  * payload kind on the current device and copies it to `out` (may be NULL).
  * Synchronous: returns after the search; the batch is left sorted.

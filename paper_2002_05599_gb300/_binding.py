@@ -204,11 +204,11 @@ def rss_sort_segments_u64(keys, vals, offsets, nseg: int | None = None, stream=N
 
 class SnTuning(ctypes.Structure):
     _fields_ = [("tile_units", ctypes.c_int), ("net_classes", ctypes.c_uint), ("rss_two_min", ctypes.c_int),
-                ("tile_stages", ctypes.c_int)]
+                ("tile_stages", ctypes.c_int), ("tile_mode", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {"tile_units": self.tile_units, "net_classes": self.net_classes, "rss_two_min": self.rss_two_min,
-                "tile_stages": self.tile_stages}
+                "tile_stages": self.tile_stages, "tile_mode": self.tile_mode}
 
 
 def _tune_lib():
@@ -234,8 +234,8 @@ def sn_tuning_get(key_bytes: int, with_vals: bool) -> dict:
 
 
 def sn_tuning_set(key_bytes: int, with_vals: bool, tile_units: int = 2048, net_classes: int = 0xF,
-                  rss_two_min: int = 160, tile_stages: int = 2) -> int:
-    t = SnTuning(tile_units, net_classes, rss_two_min, tile_stages)
+                  rss_two_min: int = 160, tile_stages: int = 2, tile_mode: int = 0) -> int:
+    t = SnTuning(tile_units, net_classes, rss_two_min, tile_stages, tile_mode)
     return _tune_lib().sn_tuning_set(key_bytes, int(with_vals), ctypes.byref(t))
 
 

@@ -40,6 +40,7 @@ struct SegTuning {
   uint32_t net_classes = 0xF;  // padded network classes in use: bit q = 2, 4, 8, 12 channels (16 always)
   int rss_two_min = 160;       // RSS segments longer than this take a 64-item sample, else 32 (16..256)
   int tile_stages = 2;         // staging depth of the tile kernel (2..4)
+  int tile_mode = 0;           // 0: task-ring tile kernel, 1: synchronous tile kernel
 };
 
 // Parameters installed for (device, key bytes, payload) (sn_tune.cu); the

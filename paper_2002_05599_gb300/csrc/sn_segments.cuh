@@ -732,8 +732,17 @@ __device__ __forceinline__ TileTasks tile_tasks(const uint16_t* cnt) {
   return t;
 }
 
+// Resident tile-kernel blocks per SM the register budget is sized for: the
+// (key, position) networks of payload sorts need about 96 registers a thread
+// (2 blocks), keys-only networks far fewer (3 blocks for u64, 4 for u32 keys),
+// and more blocks keep more tiles in flight.
+template <class K, bool kVals>
+constexpr int tile_min_blocks() {
+  return kVals ? 2 : (sizeof(K) == 4 ? 4 : 3);
+}
+
 template <class K, bool kVals, int kStages, bool kF>
-__global__ void __launch_bounds__(kTileThreads, 2)
+__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
     seg_tile_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
                     const Plan* plan, const uint32_t* __restrict__ tile_first, const uint16_t* __restrict__ counts,
                     const uint16_t* __restrict__ order, uint32_t E, unsigned* status) {
@@ -1051,6 +1060,217 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   if (stored && lane == 0) bulk_wait_all<0>();
 }
 
+// ------------------------------------------------ synchronous tile kernel --
+//
+// The second tile-kernel mode (launch parameter tile_mode = 1), built like the
+// fixed-size kernel: every warp of the block works on the same staged tile,
+// with no task ring.  Thread j of the block takes segments j, j + 256, ... of
+// the tile: a segment of 2..16 items is sorted by the lane's network, padded
+// to the largest such segment among the warp's 32 (a warp-uniform choice among
+// the enabled classes); segments of 17..32 items in the warp's window are
+// gathered by ballot and sorted two lanes each; longer ones are left to the
+// RSS kernel.  The block then stores the tile and stages its tile kStages
+// ahead into the freed buffer.
+constexpr int kSyncThreads = 256;
+
+// Bit position of the (n+1)-th set bit of m, -1 if m has at most n set bits.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+  if (__popc(m) <= n) return -1;
+  for (int q = 0; q < n; ++q) m &= m - 1;
+  return __ffs(m) - 1;
+}
+
+template <class K, bool kVals, int kStages, bool kF>
+__global__ void __launch_bounds__(kSyncThreads, tile_min_blocks<K, kVals>())
+    seg_sync_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
+                    const Plan* plan, const uint32_t* __restrict__ tile_first, uint32_t E, uint32_t net_mask,
+                    bool rss_only, unsigned* status) {
+  const TileLayout<K, kVals> lay(E);
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ TileMeta meta[kStages];
+  __shared__ int issue_failed;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t ntiles = plan->bad ? 0u : plan->ntiles;
+  const uint32_t my = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const uintptr_t kb = reinterpret_cast<uintptr_t>(keys);
+  const uintptr_t vb = reinterpret_cast<uintptr_t>(vals);
+  const uintptr_t ob = reinterpret_cast<uintptr_t>(offsets);
+
+  // Stage this block's tile number i into stage s (thread 0).  Source ranges
+  // are rounded out to 16-byte granules (a granule never crosses a page; the
+  // extra elements are read, not used, and never written back).
+  struct Where {
+    uint32_t s0, s1, e0, e1;
+  };
+  auto locate = [&](uint32_t i) -> Where {  // global loads: tile bounds, then item bounds
+    const uint32_t t = blockIdx.x + i * gridDim.x;
+    Where w;
+    w.s0 = tile_first[t];
+    w.s1 = tile_first[t + 1];
+    w.e0 = offsets[w.s0];
+    w.e1 = offsets[w.s1];
+    return w;
+  };
+  auto issue = [&](uint32_t i, int s, const Where& w) -> bool {
+    const uint32_t t = blockIdx.x + i * gridDim.x;
+    const uint32_t s0 = w.s0, s1 = w.s1, e0 = w.e0, e1 = w.e1;
+    unsigned char* stage = smem + s * lay.stage_bytes;
+    const uintptr_t oa = (ob + 4ull * s0) & ~uintptr_t(15), oz = (ob + 4ull * (s1 + 1) + 15) & ~uintptr_t(15);
+    const uintptr_t ka = (kb + sizeof(K) * e0) & ~uintptr_t(15), kz = (kb + sizeof(K) * e1 + 15) & ~uintptr_t(15);
+    uintptr_t va = 0, vz = 0;
+    TileMeta& m = meta[s];
+    m.tile = t;
+    m.s0 = s0;
+    m.s1 = s1;
+    m.e0 = e0;
+    m.e1 = e1;
+    m.off_shift = static_cast<uint32_t>((ob + 4ull * s0 - oa) / 4);
+    m.key_shift = static_cast<uint32_t>((kb + sizeof(K) * e0 - ka) / sizeof(K));
+    m.ord_shift = 0;
+    m.val_shift = 0;
+    const bool has_items = e1 > e0;
+    uint32_t bytes = static_cast<uint32_t>(oz - oa) + (has_items ? static_cast<uint32_t>(kz - ka) : 0u);
+    if constexpr (kVals) {
+      va = (vb + 4ull * e0) & ~uintptr_t(15);
+      vz = (vb + 4ull * e1 + 15) & ~uintptr_t(15);
+      m.val_shift = static_cast<uint32_t>((vb + 4ull * e0 - va) / 4);
+      if (has_items) bytes += static_cast<uint32_t>(vz - va);
+    }
+    // self-check of every copy against its staging buffer
+    const bool ok = s1 > s0 && s1 - s0 <= E && e1 >= e0 && e1 - e0 <= E + kMaxSeg &&
+                    (oz - oa) <= lay.key_at - lay.off_at && (!has_items || (kz - ka) <= lay.val_at - lay.key_at) &&
+                    (!kVals || !has_items || (vz - va) <= lay.ord_at - lay.val_at);
+    if (!ok) {
+      atomicOr(status, kStatusInternal | kCheckCopyArgs);
+      return false;
+    }
+    mbar_arrive_expect_tx(&full[s], bytes);
+    bulk_g2s(stage + lay.off_at, reinterpret_cast<const void*>(oa), static_cast<uint32_t>(oz - oa), &full[s]);
+    if (has_items) {
+      bulk_g2s(stage + lay.key_at, reinterpret_cast<const void*>(ka), static_cast<uint32_t>(kz - ka), &full[s]);
+      if constexpr (kVals)
+        bulk_g2s(stage + lay.val_at, reinterpret_cast<const void*>(va), static_cast<uint32_t>(vz - va), &full[s]);
+    }
+    return true;
+  };
+
+  uint32_t issued = 0;  // tiles staged so far (thread 0)
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+    bool ok = true;
+    while (issued < static_cast<uint32_t>(kStages) && issued < my && ok) {
+      ok = issue(issued, static_cast<int>(issued), locate(issued));
+      if (ok) ++issued;
+    }
+    issue_failed = ok ? 0 : 1;
+    if (!ok)  // let the copies already issued land, then leave
+      for (uint32_t t = 0; t < issued; ++t) (void)mbar_wait(&full[t], 0);
+  }
+  __syncthreads();
+  if (issue_failed) return;
+
+  const uint32_t key_cap = static_cast<uint32_t>((lay.val_at - lay.key_at) / sizeof(K));
+  bool failed = false;
+  uint32_t i = 0;
+  for (; i < my; ++i) {
+    const int s = static_cast<int>(i % kStages);
+    const bool ok = mbar_wait(&full[s], (i / kStages) & 1u);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const TileMeta m = meta[s];
+    // thread 0 fetches the bounds of the tile that refills this stage now, so
+    // that the refill can be issued as soon as the store has read the stage
+    Where next{};
+    if (tid == 0 && i + kStages < my) next = locate(i + kStages);
+    unsigned char* stage = smem + s * lay.stage_bytes;
+    const uint32_t* obuf = reinterpret_cast<const uint32_t*>(stage + lay.off_at) + m.off_shift;
+    K* kbuf = reinterpret_cast<K*>(stage + lay.key_at);
+    uint32_t* vbuf = reinterpret_cast<uint32_t*>(stage + lay.val_at);
+    const uint32_t ns = m.s1 - m.s0;
+    for (uint32_t base = static_cast<uint32_t>(warp) * 32; base < ns; base += kSyncThreads) {
+      const uint32_t j = base + lane;
+      uint32_t o = m.e0, L = 0;
+      if (j < ns) {
+        o = obuf[j];
+        L = obuf[j + 1] - o;
+        // self-check: the segment lies in the tile's staged items
+        if (o < m.e0 || obuf[j + 1] > m.e1 || obuf[j + 1] - m.e0 + m.key_shift > key_cap || L > kMaxSeg) {
+          atomicOr(status, kStatusInternal | kCheckSegment);
+          L = 0;
+        }
+      }
+      const int p = static_cast<int>(o - m.e0 + m.key_shift), pv = static_cast<int>(o - m.e0 + m.val_shift);
+      const bool net = L >= 2 && L <= 16;
+      const uint32_t mx = __reduce_max_sync(kFull, net ? L : 0u);
+      if (mx >= 2) {
+        const int cls = (mx <= 2 && (net_mask & 1u))    ? 2
+                        : (mx <= 4 && (net_mask & 2u))  ? 4
+                        : (mx <= 8 && (net_mask & 4u))  ? 8
+                        : (mx <= 12 && (net_mask & 8u)) ? 12
+                                                        : 16;
+        if (cls == 16) {
+          seg16<K, kVals, kF>(kbuf, vbuf, p, pv, static_cast<int>(L), net, false, lane);
+        } else if (net) {
+          if (cls == 12)
+            net_segment<12, K, kVals, kF>(kbuf, vbuf, p, pv, static_cast<int>(L));
+          else if (cls == 8)
+            net_segment<8, K, kVals, kF>(kbuf, vbuf, p, pv, static_cast<int>(L));
+          else if (cls == 4)
+            net_segment<4, K, kVals, kF>(kbuf, vbuf, p, pv, static_cast<int>(L));
+          else
+            net_segment<2, K, kVals, kF>(kbuf, vbuf, p, pv, static_cast<int>(L));
+        }
+      }
+      // 17..32: the warp's such segments, 16 at a time on lane pairs
+      unsigned pm = __ballot_sync(kFull, !rss_only && L >= 17 && L <= 32);
+      while (pm) {
+        const int src = nth_set_bit(pm, lane >> 1);
+        const bool act = src >= 0;
+        const uint32_t po = __shfl_sync(kFull, o, act ? src : 0);
+        const uint32_t pL = __shfl_sync(kFull, L, act ? src : 0);
+        seg16<K, kVals, kF>(kbuf, vbuf, static_cast<int>(po - m.e0 + m.key_shift),
+                            static_cast<int>(po - m.e0 + m.val_shift), act ? static_cast<int>(pL) : 0, act, true,
+                            lane);
+        for (int q = 0; q < 16 && pm; ++q) pm &= pm - 1;
+      }
+    }
+    fence_proxy_async_smem();  // this thread's writes, before the bulk store reads them
+    __syncthreads();
+    if (warp == 0) {
+      store_range<K>(keys, kbuf, m.key_shift, m.e0, m.e1 - m.e0, lane);
+      if constexpr (kVals) store_range<uint32_t>(vals, vbuf, m.val_shift, m.e0, m.e1 - m.e0, lane);
+      __syncwarp();
+      if (lane == 0) {
+        bulk_commit();
+        if (i + kStages < my) {
+          bulk_wait_read<0>();  // the store has read the stage
+          if (issue(i + kStages, s, next))
+            ++issued;
+          else
+            failed = true;
+        }
+      }
+    }
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      ++i;
+      break;
+    }
+  }
+  if (tid == 0) {
+    bulk_wait_all<0>();
+    if (failed) {
+      atomicOr(status, kStatusTimeout);
+      // let staged copies that were issued but not consumed land before exit
+      for (uint32_t t = i; t < issued; ++t) (void)mbar_wait(&full[t % kStages], (t / kStages) & 1u);
+    }
+  }
+}
+
 // ------------------------------------------------------------ RSS kernel ---
 
 // Stage items [e0, e0 + L) (keys and payload) into staging buffer b of the
@@ -1244,7 +1464,23 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
                                           tun.net_classes);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-  {
+  if (tun.tile_mode == 1) {
+    const TileLayout<K, kVals> lay(E);
+    const int smem_bytes = static_cast<int>(lay.total(tun.tile_stages));
+    auto kern = tun.tile_stages == 2   ? seg_sync_kernel<K, kVals, 2, kF>
+                : tun.tile_stages == 3 ? seg_sync_kernel<K, kVals, 3, kF>
+                                       : seg_sync_kernel<K, kVals, 4, kF>;
+    static std::atomic<int> cache[kCacheDevices * kCacheTileSizes * kMaxStages];
+    int per_sm = 0;
+    if ((e = blocks_per_sm(kern, kSyncThreads, smem_bytes, static_cast<int>(kTileSmemLimit),
+                           cache_slot(cache, d, E, tun.tile_stages), &per_sm)) != cudaSuccess)
+      return e;
+    const unsigned g3 = static_cast<unsigned>(
+        std::max<uint64_t>(1, std::min<uint64_t>(sl.cap - 1, static_cast<uint64_t>(d.sm_count) * per_sm)));
+    kern<<<g3, kSyncThreads, smem_bytes, stream>>>(keys, vals, offsets, plan, tile_first, E, tun.net_classes,
+                                                   rss_only, d.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
     const TileLayout<K, kVals> lay(E);
     const int smem_bytes = static_cast<int>(lay.total(tun.tile_stages));
     auto kern = tun.tile_stages == 2   ? seg_tile_kernel<K, kVals, 2, kF>
@@ -1284,7 +1520,8 @@ template <class K, bool kF = false>
 cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,
                             void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
                             const DeviceInfo& d) {
-  if (t.tile_units < 512 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg || t.net_classes > 0xFu)
+  if (t.tile_units < 512 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg || t.net_classes > 0xFu ||
+      t.tile_mode < 0 || t.tile_mode > 1)
     return cudaErrorInvalidValue;
   if (!(vals ? tile_fits<K, true>(t.tile_units, t.tile_stages) : tile_fits<K, false>(t.tile_units, t.tile_stages)))
     return cudaErrorInvalidValue;

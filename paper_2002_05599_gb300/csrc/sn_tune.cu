@@ -29,7 +29,8 @@ bool g_touched[kDevs][2][2];
 
 bool tuning_valid(const SegTuning& t) {
   return t.tile_units >= 512 && t.tile_units <= 8192 && t.net_classes <= 0xFu && t.rss_two_min >= 16 &&
-         t.rss_two_min <= SN_MAX_SEGMENT && t.tile_stages >= 2 && t.tile_stages <= 4;
+         t.rss_two_min <= SN_MAX_SEGMENT && t.tile_stages >= 2 && t.tile_stages <= 4 && t.tile_mode >= 0 &&
+         t.tile_mode <= 1;
 }
 
 SegTuning current_tuning(int device, int key_bytes, bool vals) {
@@ -52,6 +53,7 @@ sn_tuning to_c(const SegTuning& t) {
   c.net_classes = t.net_classes;
   c.rss_two_min = t.rss_two_min;
   c.tile_stages = t.tile_stages;
+  c.tile_mode = t.tile_mode;
   return c;
 }
 
@@ -61,6 +63,7 @@ SegTuning from_c(const sn_tuning& c) {
   t.net_classes = c.net_classes;
   t.rss_two_min = c.rss_two_min;
   t.tile_stages = c.tile_stages;
+  t.tile_mode = c.tile_mode;
   return t;
 }
 
@@ -185,6 +188,13 @@ int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64
   static const int kStagesC[] = {2, 3, 4};
   static const int kTwo[] = {32, 64, 96, 128, 160, 192, 224, 256};
   for (int pass = 0; pass < 2 && !failed; ++pass) {
+    for (int mode = 0; mode <= 1 && !failed; ++mode) {
+      if (mode == best.tile_mode) continue;
+      sn::SegTuning c = best;
+      c.tile_mode = mode;
+      const float t = time_of(c);
+      if (t < 0.99f * best_t) best = c, best_t = t;
+    }
     for (unsigned mask = 0; mask <= 0xFu && !failed; ++mask) {
       sn::SegTuning c = best;
       c.net_classes = mask;
@@ -229,7 +239,7 @@ int sn_tuning_save(const char* path) {
   if (path == nullptr) return SN_EINVAL;
   FILE* f = std::fopen(path, "w");
   if (f == nullptr) return SN_EINVAL;
-  bool ok = std::fprintf(f, "smallsort-tuning 2\n") > 0;
+  bool ok = std::fprintf(f, "smallsort-tuning 3\n") > 0;
   {
     std::lock_guard<std::mutex> lk(sn::g_mu);
     for (int dev = 0; dev < sn::kDevs; ++dev)
@@ -237,8 +247,8 @@ int sn_tuning_save(const char* path) {
         for (int v = 0; v < 2; ++v)
           if (sn::g_touched[dev][u64][v]) {
             const sn::SegTuning& t = sn::g_table[dev][u64][v];
-            ok = ok && std::fprintf(f, "%d %d %d %d %u %d %d\n", dev, u64 ? 8 : 4, v, t.tile_units,
-                                    t.net_classes, t.rss_two_min, t.tile_stages) > 0;
+            ok = ok && std::fprintf(f, "%d %d %d %d %u %d %d %d\n", dev, u64 ? 8 : 4, v, t.tile_units,
+                                    t.net_classes, t.rss_two_min, t.tile_stages, t.tile_mode) > 0;
           }
   }
   ok = (std::fclose(f) == 0) && ok;
@@ -250,7 +260,7 @@ int sn_tuning_load(const char* path) {
   FILE* f = std::fopen(path, "r");
   if (f == nullptr) return SN_EINVAL;
   int version = 0;
-  if (std::fscanf(f, "smallsort-tuning %d\n", &version) != 1 || version != 2) {
+  if (std::fscanf(f, "smallsort-tuning %d\n", &version) != 1 || version != 3) {
     std::fclose(f);
     return SN_EINVAL;
   }
@@ -259,15 +269,16 @@ int sn_tuning_load(const char* path) {
     cudaGetLastError();
     ndev = 0;
   }
-  int dev, kb, v, tu, two, st;
+  int dev, kb, v, tu, two, st, mode;
   unsigned mask;
   int rc = SN_OK, n;
-  while ((n = std::fscanf(f, "%d %d %d %d %u %d %d", &dev, &kb, &v, &tu, &mask, &two, &st)) == 7) {
+  while ((n = std::fscanf(f, "%d %d %d %d %u %d %d %d", &dev, &kb, &v, &tu, &mask, &two, &st, &mode)) == 8) {
     sn::SegTuning t;
     t.tile_units = tu;
     t.net_classes = mask;
     t.rss_two_min = two;
     t.tile_stages = st;
+    t.tile_mode = mode;
     if (dev < 0 || dev >= sn::kDevs || (kb != 4 && kb != 8) || (v != 0 && v != 1) || !sn::tuning_valid(t) ||
         !sn::tile_fits(kb, v != 0, t.tile_units, t.tile_stages)) {
       rc = SN_EINVAL;

@@ -119,12 +119,13 @@ def test_tuning_argument_errors_and_file_format(lib, tmp_path):
     import paper_2002_05599_gb300 as sn
     from paper_2002_05599_gb300._binding import SnTuning
     L = sn._binding._tune_lib()
-    t = SnTuning(2048, 0xF, 160, 2)
+    t = SnTuning(2048, 0xF, 160, 2, 0)
     assert L.sn_tuning_set(2, 0, ctypes.byref(t)) == -1            # key_bytes
     assert L.sn_tuning_get(4, 0, None) == -1
-    for bad in (SnTuning(256, 0xF, 160, 2), SnTuning(16384, 0xF, 160, 2), SnTuning(2048, 0x10, 160, 2),
-                SnTuning(2048, 0xF, 8, 2), SnTuning(2048, 0xF, 300, 2), SnTuning(2048, 0xF, 160, 1),
-                SnTuning(2048, 0xF, 160, 5), SnTuning(8192, 0xF, 160, 2)):  # last: staging too large
+    for bad in (SnTuning(256, 0xF, 160, 2, 0), SnTuning(16384, 0xF, 160, 2, 0), SnTuning(2048, 0x10, 160, 2, 0),
+                SnTuning(2048, 0xF, 8, 2, 0), SnTuning(2048, 0xF, 300, 2, 0), SnTuning(2048, 0xF, 160, 1, 0),
+                SnTuning(2048, 0xF, 160, 5, 0), SnTuning(2048, 0xF, 160, 2, 2),
+                SnTuning(8192, 0xF, 160, 2, 0)):  # last: staging too large
         assert L.sn_tuning_set(4, 1, ctypes.byref(bad)) == -1
     L.sn_tune_segments.argtypes = L.sn_tune_segments.argtypes
     assert L.sn_tune_segments(None, None, None, 5, 4, None, None, None) == -1
@@ -132,19 +133,19 @@ def test_tuning_argument_errors_and_file_format(lib, tmp_path):
     assert sn.sn_tuning_save(os.path.join(tmp_path, "no", "such", "dir.txt")) == -1
     bad_file = os.path.join(tmp_path, "bad.txt")
     with open(bad_file, "w") as f:
-        f.write("smallsort-tuning 2\n0 4 0 2048 15 160\n")  # truncated line
+        f.write("smallsort-tuning 3\n0 4 0 2048 15 160 2\n")  # truncated line
     assert sn.sn_tuning_load(bad_file) == -1
     with open(bad_file, "w") as f:
-        f.write("smallsort-tuning 2\n0 4 0 100 15 160 2\n")  # tile size out of range
+        f.write("smallsort-tuning 3\n0 4 0 100 15 160 2 0\n")  # tile size out of range
     assert sn.sn_tuning_load(bad_file) == -1
     with open(bad_file, "w") as f:
-        f.write("smallsort-tuning 2\n0 8 1 4096 15 160 4\n")  # four 4096-unit stages do not fit
+        f.write("smallsort-tuning 3\n0 8 1 4096 15 160 4 0\n")  # four 4096-unit stages do not fit
     assert sn.sn_tuning_load(bad_file) == -1
     with open(bad_file, "w") as f:
-        f.write("smallsort-tuning 1\n0 4 0 2048 15 160\n")  # old format
+        f.write("smallsort-tuning 2\n0 4 0 2048 15 160 2\n")  # old format
     assert sn.sn_tuning_load(bad_file) == -1
     assert sn.sn_tuning_load(os.path.join(tmp_path, "missing.txt")) == -1
     good = os.path.join(tmp_path, "good.txt")
     with open(good, "w") as f:
-        f.write("smallsort-tuning 2\n0 4 0 4096 5 128 2\n0 8 1 1024 15 192 4\n")
+        f.write("smallsort-tuning 3\n0 4 0 4096 5 128 2 1\n0 8 1 1024 15 192 4 0\n")
     assert sn.sn_tuning_load(good) == 0  # entries for devices that are not present are skipped

@@ -11,11 +11,12 @@ from gpu_util import to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-SETS = [dict(tile_units=512, net_classes=0x0, rss_two_min=16, tile_stages=2),
-        dict(tile_units=4096, net_classes=0xF, rss_two_min=256, tile_stages=2),
-        dict(tile_units=1024, net_classes=0x5, rss_two_min=64, tile_stages=4),
-        dict(tile_units=2048, net_classes=0xA, rss_two_min=200, tile_stages=3),
-        dict(tile_units=512, net_classes=0x4, rss_two_min=128, tile_stages=3)]
+SETS = [dict(tile_units=512, net_classes=0x0, rss_two_min=16, tile_stages=2, tile_mode=0),
+        dict(tile_units=4096, net_classes=0xF, rss_two_min=256, tile_stages=2, tile_mode=1),
+        dict(tile_units=1024, net_classes=0x5, rss_two_min=64, tile_stages=4, tile_mode=0),
+        dict(tile_units=2048, net_classes=0xA, rss_two_min=200, tile_stages=3, tile_mode=1),
+        dict(tile_units=512, net_classes=0x4, rss_two_min=128, tile_stages=3, tile_mode=1),
+        dict(tile_units=1024, net_classes=0x0, rss_two_min=160, tile_stages=4, tile_mode=1)]
 
 
 @pytest.fixture
@@ -76,3 +77,22 @@ def test_autotuner_installs_its_choice_and_sorts(tmp_path, restore_defaults):
     sn.check(sn.sn_tuning_set(8, True), "reset")
     assert sn.sn_tuning_load(path) == sn.SN_OK
     assert sn.sn_tuning_get(8, True) == params
+
+
+@pytest.mark.parametrize("dtype,with_vals", [(np.uint64, True), (np.uint32, False), (np.uint32, True), (np.uint64, False)])
+@pytest.mark.parametrize("lengths,lo,hi", [("geometric", 1, 256), ("uniform", 0, 40)])
+def test_synchronous_tile_mode_many_tiles(dtype, with_vals, lengths, lo, hi, restore_defaults):
+    # the synchronous tile kernel over enough tiles that every block reuses its stages
+    kb = np.dtype(dtype).itemsize
+    fn = sn.sn_sort_segments_u64 if kb == 8 else sn.sn_sort_segments
+    for stages, units in ((2, 2048), (3, 1024), (4, 512)):
+        sn.check(sn.sn_tuning_set(kb, with_vals, tile_units=units, tile_stages=stages, tile_mode=1), "set")
+        for keys in ("uniform", "fewdistinct"):
+            k, v, off = wl.segment_batch(1 << 17, lengths, keys, dtype, with_vals, seed=80 + stages, lo=lo, hi=hi)
+            ek, ev = oracle.sort_segments(k, v, off)
+            dk, dv = to_dev(k), (to_dev(v) if with_vals else None)
+            sn.check(fn(dk, dv, to_dev(off)), "sort")
+            assert sn.sn_check() == sn.SN_OK
+            assert np.array_equal(to_host(dk, dtype), ek)
+            if with_vals:
+                assert np.array_equal(to_host(dv, np.uint32), ev)
