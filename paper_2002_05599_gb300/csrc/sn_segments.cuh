@@ -158,16 +158,17 @@ template <> struct RssMem<uint64_t, true> {
   }
 };
 
-// Per-warp region of the RSS kernel: two staging buffers (keys, payload),
-// two mbarriers, the RSS scratch.
+// Per-warp region of the RSS kernel: kRssBufs staging buffers (keys, payload)
+// with one mbarrier each, the RSS scratch.
+constexpr int kRssBufs = 3;
 template <class K, bool kVals>
 struct RssWarpLayout {
   static constexpr size_t kKeyCap = (kMaxSeg + 2 * (16 / sizeof(K))) * sizeof(K);
   static constexpr size_t kValCap = kVals ? (kMaxSeg + 8) * 4 : 0;
   static constexpr size_t kBar = 0;
-  static constexpr size_t kKeys = 16;
-  static constexpr size_t kVals_ = kKeys + 2 * kKeyCap;
-  static constexpr size_t kScratch = (kVals_ + 2 * kValCap + 15) & ~static_cast<size_t>(15);
+  static constexpr size_t kKeys = 32;
+  static constexpr size_t kVals_ = kKeys + kRssBufs * kKeyCap;
+  static constexpr size_t kScratch = (kVals_ + kRssBufs * kValCap + 15) & ~static_cast<size_t>(15);
   static constexpr size_t kBytes = (kScratch + RssMem<K, kVals>::kBytes + 127) & ~static_cast<size_t>(127);
 };
 
@@ -918,7 +919,12 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
         __nanosleep(64);
       }
     }
-    if (failed && lane == 0) atomicOr(status, kStatusTimeout);
+    if (failed && lane == 0) {
+      atomicOr(status, kStatusTimeout);
+      // staged tiles whose work was never published: let their copies land
+      // (bounded waits) before the block can exit
+      for (uint32_t x = pushed; x < issued; ++x) (void)mbar_wait(&full[x % kStages], (x / kStages) & 1u);
+    }
     // one stop item per consumer warp
     for (uint32_t i = lane; i < kTileWarps; i += 32) ring[(tail + i) & (kRing - 1)] = kRingDone;
     __syncwarp();
@@ -1311,8 +1317,7 @@ __global__ void __launch_bounds__(kRssThreads, 2)
   uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + WL::kBar);
   const RssMem<K, kVals> rm(wbase + WL::kScratch);
   if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < kRssBufs; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
   }
   __syncwarp();
@@ -1320,17 +1325,19 @@ __global__ void __launch_bounds__(kRssThreads, 2)
   const uint32_t gw = blockIdx.x * kRssWarps + warp;
   const uint32_t W = gridDim.x * kRssWarps;
 
-  // Segment number d of this warp lives in staging buffer d & 1; its mbarrier
-  // phase is (d >> 1) & 1.  A segment is staged one step before it is sorted.
-  uint32_t issued = 0;
+  // Segment number d of this warp lives in staging buffer d % kRssBufs; its
+  // mbarrier phase is (d / kRssBufs) & 1.  A segment is staged one step before
+  // it is sorted, and its store has two segments' time to read the buffer
+  // before the buffer is staged again.
+  uint32_t issued = 0, sorted = 0;
   bool failed = false;
   uint32_t pe0 = 0, pL = 0;  // the staged, not yet sorted segment (issued - 1)
 
   auto sort_staged = [&](uint32_t d) {  // sort segment number d of this warp
-    const int b = d & 1;
+    const int b = static_cast<int>(d % kRssBufs);
     // every lane waits itself (bulk-copy data is visible to the lanes that
     // observe the phase); a timeout anywhere fails the whole warp
-    if (!__all_sync(kFull, mbar_wait(&bar[b], (d >> 1) & 1u))) {
+    if (!__all_sync(kFull, mbar_wait(&bar[b], (d / kRssBufs) & 1u))) {
       if (lane == 0) atomicOr(status, kStatusTimeout);
       failed = true;
       return;
@@ -1345,11 +1352,9 @@ __global__ void __launch_bounds__(kRssThreads, 2)
     __syncwarp();
     store_range<K>(keys, kbuf, ks, pe0, pL, lane);
     if constexpr (kVals) store_range<uint32_t>(vals, vbuf, vs, pe0, pL, lane);
-    if (lane == 0) {
-      bulk_commit();
-      bulk_wait_read<0>();  // the buffer is staged again two segments later
-    }
+    if (lane == 0) bulk_commit();
     __syncwarp();
+    sorted = d + 1;
   };
 
   for (uint32_t chunk = gw; chunk < ntiles && !failed; chunk += 32u * W) {
@@ -1381,7 +1386,13 @@ __global__ void __launch_bounds__(kRssThreads, 2)
         m &= m - 1;
         const uint32_t ne0 = __shfl_sync(kFull, e0q, r), nL = __shfl_sync(kFull, Lq, r);
         // stage segment number `issued`, then sort the previous one while it loads
-        if (lane == 0) rss_issue<K, kVals>(wbase, issued & 1, &bar[issued & 1], keys, vals, ne0, nL);
+        if (lane == 0) {
+          // the store of segment issued - kRssBufs (the last but one committed)
+          // must have read this buffer
+          if (issued >= static_cast<uint32_t>(kRssBufs)) bulk_wait_read<1>();
+          const int nb = static_cast<int>(issued % kRssBufs);
+          rss_issue<K, kVals>(wbase, nb, &bar[nb], keys, vals, ne0, nL);
+        }
         ++issued;
         if (issued >= 2) sort_staged(issued - 2);
         pe0 = ne0;
@@ -1390,7 +1401,12 @@ __global__ void __launch_bounds__(kRssThreads, 2)
     }
   }
   if (issued >= 1 && !failed) sort_staged(issued - 1);
-  if (lane == 0) bulk_wait_all<0>();
+  if (lane == 0) {
+    bulk_wait_all<0>();
+    // after a failure, let staged copies that were never sorted land (bounded waits)
+    if (failed)
+      for (uint32_t x = sorted; x < issued; ++x) (void)mbar_wait(&bar[x % kRssBufs], (x / kRssBufs) & 1u);
+  }
 }
 
 // ------------------------------------------------------------ host side ----
