@@ -178,7 +178,10 @@ int sn_sort_segments_u64_noalloc(uint64_t *keys, uint32_t *vals, const uint32_t 
 typedef struct {
     int tile_units;        /* segments + items per tile of the network kernel: 512..8192 (default 2048) */
     unsigned net_classes;  /* padded network sizes for 2..16-item segments: bit 0 = 2, bit 1 = 4,
-                              bit 2 = 8, bit 3 = 12 channels; 16 channels always (default 0xF) */
+                              bit 2 = 8, bit 3 = 12 channels; 16 channels always.  Bit 4: segments
+                              of 33..64 items take a 64-channel warp network instead of Register
+                              Sample Sort (sn_sort_segments* and the server only; the rss_* calls
+                              always use Register Sample Sort).  Default 0x1F */
     int rss_two_min;       /* Register Sample Sort: segments longer than this draw a 64-item sample,
                               shorter ones 32 (16..256, default 160) */
     int tile_stages;       /* staging depth of the network kernel: 2..4 tiles in flight per block

@@ -103,10 +103,12 @@ __device__ __forceinline__ void ce(KeyIdx<K>& a, KeyIdx<K>& b) {
   a = lo;
   b = hi;
 }
-// Adjacent items with equal keys out of position order.
+// Adjacent items with equal keys out of position order, where the later one
+// is a real item (position below `real`): padding items share the maximum key
+// and may end in any order among themselves, which does not matter.
 template <class K>
-__device__ __forceinline__ bool tie_misordered(const KeyIdx<K>& a, const KeyIdx<K>& b) {
-  return a.k == b.k && a.ix > b.ix;
+__device__ __forceinline__ bool tie_misordered(const KeyIdx<K>& a, const KeyIdx<K>& b, uint32_t real) {
+  return a.k == b.k && a.ix > b.ix && b.ix < real;
 }
 
 // Min/max of two items for the warp network: `keep_min` selects the result.

@@ -37,7 +37,8 @@ enum class SegMode : int { kNetworkWarpRss = 0, kRssOnly = 1 };
 
 struct SegTuning {
   int tile_units = 2048;       // segments + elements per tile (512..8192)
-  uint32_t net_classes = 0xF;  // padded network classes in use: bit q = 2, 4, 8, 12 channels (16 always)
+  uint32_t net_classes = 0x1F;  // bits 0..3: padded classes 2, 4, 8, 12 channels (16 always);
+                                // bit 4: 64-channel warp network for 33..64 items
   int rss_two_min = 160;       // RSS segments longer than this take a 64-item sample, else 32 (16..256)
   int tile_stages = 2;         // staging depth of the tile kernel (2..4)
   int tile_mode = 0;           // 0: task-ring tile kernel, 1: synchronous tile kernel

@@ -273,7 +273,7 @@ __device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int 
     Net<N>::run(it);
     bool tie = false;
 #pragma unroll
-    for (int q = 0; q + 1 < N; ++q) tie |= tie_misordered(it[q], it[q + 1]);
+    for (int q = 0; q + 1 < N; ++q) tie |= tie_misordered(it[q], it[q + 1], static_cast<uint32_t>(L));
     if (tie) {
       using IO = ItemOf<K>;
       typename IO::T full[N];
@@ -375,10 +375,10 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
     if (pair) pair_merge(x, upper);
     bool tie = false;
 #pragma unroll
-    for (int q = 0; q < 15; ++q) tie |= tie_misordered(x[q], x[q + 1]);
+    for (int q = 0; q < 15; ++q) tie |= tie_misordered(x[q], x[q + 1], static_cast<uint32_t>(L));
     if (pair) {  // the boundary between the even lane's last item and the odd lane's first
       const KeyIdx<K> prev = shfl_xor(x[15], 1);
-      if (upper) tie |= tie_misordered(prev, x[0]);
+      if (upper) tie |= tie_misordered(prev, x[0], static_cast<uint32_t>(L));
     }
     if (__any_sync(kFull, tie)) {
       using IO = ItemOf<K>;
@@ -422,19 +422,37 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
 template <int N, class K, bool kVals>
 __device__ __forceinline__ void bucket_network(const RssMem<K, kVals>& rm, int st, int c) {
   using IO = RssIO<K, kVals>;
-  if constexpr (kVals) {
-    typename IO::T it[N];
+  if constexpr (kVals && sizeof(K) == 8) {
+    // 8-byte keys with positions: key-first network with the positions
+    // carried; a (key, position) pass only when equal keys were left out of
+    // position order
+    KeyIdx<K> it[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) it[q] = q < c ? rm.get(st + q) : IO::sentinel(q);
+    for (int q = 0; q < N; ++q) {
+      const typename IO::T x = q < c ? rm.get(st + q) : IO::sentinel(q);
+      it[q] = KeyIdx<K>{IO::key(x), IO::idx(x)};
+    }
     Net<N>::run(it);
+    bool tie = false;
+#pragma unroll
+    for (int q = 0; q + 1 < N; ++q) tie |= tie_misordered(it[q], it[q + 1], 0x10000u);  // sentinels: 0x10000 + slot
+    if (tie) {
+      typename IO::T full[N];
+#pragma unroll
+      for (int q = 0; q < N; ++q) full[q] = IO::make(it[q].k, it[q].ix);
+      Net<N>::run(full);
+#pragma unroll
+      for (int q = 0; q < N; ++q) it[q] = KeyIdx<K>{IO::key(full[q]), IO::idx(full[q])};
+    }
 #pragma unroll
     for (int q = 0; q < N; ++q)
-      if (q < c) rm.set(st + q, it[q]);
+      if (q < c) rm.set(st + q, IO::make(it[q].k, it[q].ix));
   } else {
-    // keys only: equal keys are interchangeable
-    K k[N];
+    // bare keys (equal keys are interchangeable), or 4-byte keys packed with
+    // their positions into one 64-bit word that a single min/max orders
+    typename IO::T k[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) k[q] = q < c ? rm.get(st + q) : static_cast<K>(~static_cast<K>(0));
+    for (int q = 0; q < N; ++q) k[q] = q < c ? rm.get(st + q) : IO::sentinel(q);
     Net<N>::run(k);
 #pragma unroll
     for (int q = 0; q < N; ++q)
@@ -482,6 +500,50 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K, kVals>& rm, in
   }
 }
 
+// Segments of 33..64 items outside the RSS-only calls (launch parameter
+// net_classes bit 4): a 64-channel warp network, two items per lane, in place
+// of Register Sample Sort, whose sample sort and classification cost more
+// than the whole network at this size.  Item e = 32 r + lane starts in
+// register r; the 32-lane network sorts each register column, then slot l
+// meets slot 63 - l (the smaller items form a bitonic lower half, the larger
+// a bitonic upper half in lane order) and the half-cleaners 16, 8, 4, 2, 1
+// sort each half, leaving sorted slot 32 r + lane in register r.  With a
+// payload the items are (key, position) pairs, so equal keys keep their
+// input order.
+template <class K, bool kVals, bool kF>
+__device__ __forceinline__ void net64_segment(const K* kbuf, const uint32_t* vbuf, int p, int pv, int L, int lane,
+                                              K* __restrict__ gk, uint32_t* __restrict__ gv) {
+  using IO = RssIO<K, kVals>;
+  using It = typename IO::T;
+  const int e1 = 32 + lane;
+  It lo = lane < L ? IO::make(key_enc<K, kF>(kbuf[p + lane]), static_cast<uint32_t>(lane))
+                   : IO::sentinel(static_cast<uint32_t>(lane));
+  It hi = e1 < L ? IO::make(key_enc<K, kF>(kbuf[p + e1]), static_cast<uint32_t>(e1))
+                 : IO::sentinel(static_cast<uint32_t>(e1));
+  warp_network32(lo, lane);
+  warp_network32(hi, lane);
+  {
+    const It y = shfl_idx(hi, 31 - lane);
+    hi = pick(lo, y, false);
+    lo = pick(lo, y, true);
+  }
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const bool keep_min = (lane & m) == 0;
+    const It a = shfl_xor(lo, m), b = shfl_xor(hi, m);
+    lo = pick(lo, a, keep_min);
+    hi = pick(hi, b, keep_min);
+  }
+  if (lane < L) {
+    gk[lane] = key_dec<K, kF>(IO::key(lo));
+    if constexpr (kVals) gv[lane] = vbuf[pv + IO::idx(lo)];
+  }
+  if (e1 < L) {
+    gk[e1] = key_dec<K, kF>(IO::key(hi));
+    if constexpr (kVals) gv[e1] = vbuf[pv + IO::idx(hi)];
+  }
+}
+
 // Register Sample Sort of one segment of L (17..256) items by one warp
 // (Sec. 3).  Splitters and classification use the keys alone; the buckets
 // then hold (key, position-in-segment) items and are sorted by both, so equal
@@ -504,8 +566,9 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K, kVals>& rm, in
 //     or a bitonic pass in shared memory above 32);
 //  7. write back (payload gathered by original position).
 template <class K, bool kVals, bool kF>
-__device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L,
-                                            const RssMem<K, kVals>& rm, int lane, int two_min) {
+__device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf, int p, int pv, int L,
+                                            const RssMem<K, kVals>& rm, int lane, int two_min,
+                                            K* __restrict__ gk, uint32_t* __restrict__ gv) {
   using IO = RssIO<K, kVals>;
   using It = typename IO::T;
   constexpr K kTop = static_cast<K>(~static_cast<K>(0));
@@ -658,29 +721,16 @@ __device__ __forceinline__ void rss_segment(K* kbuf, uint32_t* vbuf, int p, int 
     __syncwarp();
   }
 
-  // 7. write back (payload gathered by original position)
-  if constexpr (kVals) {
-    uint32_t vv[8];
+  // 7. write the sorted segment straight to its place in global memory
+  //    (coalesced: lane l writes items 32 r + l; payload gathered by
+  //    original position from the staged copy)
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int e = (r << 5) + lane;
-      if (r < rounds && e < L) {
-        const It y = rm.get(e);
-        kbuf[p + e] = key_dec<K, kF>(IO::key(y));
-        vv[r] = vbuf[pv + IO::idx(y)];
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int e = (r << 5) + lane;
-      if (r < rounds && e < L) vbuf[pv + e] = vv[r];
-    }
-  } else {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int e = (r << 5) + lane;
-      if (r < rounds && e < L) kbuf[p + e] = key_dec<K, kF>(IO::key(rm.get(e)));
+  for (int r = 0; r < 8; ++r) {
+    const int e = (r << 5) + lane;
+    if (r < rounds && e < L) {
+      const It y = rm.get(e);
+      gk[e] = key_dec<K, kF>(IO::key(y));
+      if constexpr (kVals) gv[e] = vbuf[pv + IO::idx(y)];
     }
   }
   __syncwarp();
@@ -1304,11 +1354,20 @@ __device__ __forceinline__ void rss_issue(unsigned char* wbase, int b, uint64_t*
              static_cast<uint32_t>(vz - va), bar);
 }
 
+// Resident RSS blocks per SM the register budget is sized for: the kernel is
+// latency-bound (shuffle and shared-memory round trips), so as many warps as
+// fit without spills (4-byte bare keys 62 registers a thread, 4-byte keys with
+// payload and 8-byte bare keys about 80, 8-byte keys with payload 116).
+template <class K, bool kVals>
+constexpr int rss_min_blocks() {
+  return sizeof(K) == 4 ? (kVals ? 3 : 4) : (kVals ? 2 : 3);
+}
+
 template <class K, bool kVals, bool kF>
-__global__ void __launch_bounds__(kRssThreads, 2)
+__global__ void __launch_bounds__(kRssThreads, rss_min_blocks<K, kVals>())
     seg_rss_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
                    const Plan* plan, const uint32_t* __restrict__ tile_first, const uint16_t* __restrict__ counts,
-                   const uint16_t* __restrict__ order, int two_min, unsigned* status) {
+                   const uint16_t* __restrict__ order, int two_min, bool net64, unsigned* status) {
   using WL = RssWarpLayout<K, kVals>;
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
@@ -1326,15 +1385,18 @@ __global__ void __launch_bounds__(kRssThreads, 2)
   const uint32_t W = gridDim.x * kRssWarps;
 
   // Segment number d of this warp lives in staging buffer d % kRssBufs; its
-  // mbarrier phase is (d / kRssBufs) & 1.  A segment is staged one step before
-  // it is sorted, and its store has two segments' time to read the buffer
-  // before the buffer is staged again.
+  // mbarrier phase is (d / kRssBufs) & 1, and lane d % kRssBufs keeps its
+  // start and length.  Segment d is sorted just before segment d + kRssBufs
+  // is staged into the same buffer, so kRssBufs - 1 segments load while one
+  // is sorted; results go straight to global memory, so a buffer is free as
+  // soon as its sort ends.
   uint32_t issued = 0, sorted = 0;
   bool failed = false;
-  uint32_t pe0 = 0, pL = 0;  // the staged, not yet sorted segment (issued - 1)
+  uint32_t q_e0 = 0, q_L = 0;
 
   auto sort_staged = [&](uint32_t d) {  // sort segment number d of this warp
     const int b = static_cast<int>(d % kRssBufs);
+    const uint32_t pe0 = __shfl_sync(kFull, q_e0, b), pL = __shfl_sync(kFull, q_L, b);
     // every lane waits itself (bulk-copy data is visible to the lanes that
     // observe the phase); a timeout anywhere fails the whole warp
     if (!__all_sync(kFull, mbar_wait(&bar[b], (d / kRssBufs) & 1u))) {
@@ -1342,17 +1404,19 @@ __global__ void __launch_bounds__(kRssThreads, 2)
       failed = true;
       return;
     }
-    K* kbuf = reinterpret_cast<K*>(wbase + WL::kKeys + b * WL::kKeyCap);
-    uint32_t* vbuf = reinterpret_cast<uint32_t*>(wbase + WL::kVals_ + b * WL::kValCap);
+    const K* kbuf = reinterpret_cast<const K*>(wbase + WL::kKeys + b * WL::kKeyCap);
+    const uint32_t* vbuf = reinterpret_cast<const uint32_t*>(wbase + WL::kVals_ + b * WL::kValCap);
     const uint32_t ks = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(keys + pe0) & 15) / sizeof(K));
     const uint32_t vs = kVals ? static_cast<uint32_t>((reinterpret_cast<uintptr_t>(vals + pe0) & 15) / 4) : 0u;
-    rss_segment<K, kVals, kF>(kbuf, vbuf, static_cast<int>(ks), static_cast<int>(vs), static_cast<int>(pL), rm, lane,
-                          two_min);
-    fence_proxy_async_smem();
-    __syncwarp();
-    store_range<K>(keys, kbuf, ks, pe0, pL, lane);
-    if constexpr (kVals) store_range<uint32_t>(vals, vbuf, vs, pe0, pL, lane);
-    if (lane == 0) bulk_commit();
+    uint32_t* gv = kVals ? vals + pe0 : nullptr;
+    if (net64 && pL <= 64)
+      net64_segment<K, kVals, kF>(kbuf, vbuf, static_cast<int>(ks), static_cast<int>(vs), static_cast<int>(pL), lane,
+                                  keys + pe0, gv);
+    else
+      rss_segment<K, kVals, kF>(kbuf, vbuf, static_cast<int>(ks), static_cast<int>(vs), static_cast<int>(pL), rm,
+                                lane, two_min, keys + pe0, gv);
+    // every lane's reads of the staged copy are done (the results went
+    // straight to global memory), so the buffer may be staged again
     __syncwarp();
     sorted = d + 1;
   };
@@ -1385,24 +1449,24 @@ __global__ void __launch_bounds__(kRssThreads, 2)
         const int r = __ffs(m) - 1;
         m &= m - 1;
         const uint32_t ne0 = __shfl_sync(kFull, e0q, r), nL = __shfl_sync(kFull, Lq, r);
-        // stage segment number `issued`, then sort the previous one while it loads
-        if (lane == 0) {
-          // the store of segment issued - kRssBufs (the last but one committed)
-          // must have read this buffer
-          if (issued >= static_cast<uint32_t>(kRssBufs)) bulk_wait_read<1>();
-          const int nb = static_cast<int>(issued % kRssBufs);
-          rss_issue<K, kVals>(wbase, nb, &bar[nb], keys, vals, ne0, nL);
+        // free the buffer (sort its segment), then stage segment `issued` into it
+        if (issued >= static_cast<uint32_t>(kRssBufs)) {
+          sort_staged(issued - kRssBufs);
+          if (failed) break;
+        }
+        const int nb = static_cast<int>(issued % kRssBufs);
+        if (lane == 0) rss_issue<K, kVals>(wbase, nb, &bar[nb], keys, vals, ne0, nL);
+        if (lane == nb) {
+          q_e0 = ne0;
+          q_L = nL;
         }
         ++issued;
-        if (issued >= 2) sort_staged(issued - 2);
-        pe0 = ne0;
-        pL = nL;
       }
     }
   }
-  if (issued >= 1 && !failed) sort_staged(issued - 1);
+  for (uint32_t d = issued > static_cast<uint32_t>(kRssBufs) ? issued - kRssBufs : 0u; d < issued && !failed; ++d)
+    sort_staged(d);
   if (lane == 0) {
-    bulk_wait_all<0>();
     // after a failure, let staged copies that were never sorted land (bounded waits)
     if (failed)
       for (uint32_t x = sorted; x < issued; ++x) (void)mbar_wait(&bar[x % kRssBufs], (x / kRssBufs) & 1u);
@@ -1526,7 +1590,8 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
     const unsigned g4 = static_cast<unsigned>(std::max<uint64_t>(
         1, std::min<uint64_t>((tiles_cap + kRssWarps - 1) / kRssWarps, static_cast<uint64_t>(d.sm_count) * per_sm)));
     kern<<<g4, kRssThreads, smem_bytes, stream>>>(keys, vals, offsets, plan, tile_first, counts, order,
-                                                   tun.rss_two_min, d.status);
+                                                   tun.rss_two_min, !rss_only && (tun.net_classes & 0x10u),
+                                                   d.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1536,7 +1601,7 @@ template <class K, bool kF = false>
 cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,
                             void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
                             const DeviceInfo& d) {
-  if (t.tile_units < 512 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg || t.net_classes > 0xFu ||
+  if (t.tile_units < 512 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg || t.net_classes > 0x1Fu ||
       t.tile_mode < 0 || t.tile_mode > 1)
     return cudaErrorInvalidValue;
   if (!(vals ? tile_fits<K, true>(t.tile_units, t.tile_stages) : tile_fits<K, false>(t.tile_units, t.tile_stages)))

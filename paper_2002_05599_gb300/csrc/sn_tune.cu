@@ -28,7 +28,7 @@ bool g_touched[kDevs][2][2];
 }  // namespace
 
 bool tuning_valid(const SegTuning& t) {
-  return t.tile_units >= 512 && t.tile_units <= 8192 && t.net_classes <= 0xFu && t.rss_two_min >= 16 &&
+  return t.tile_units >= 512 && t.tile_units <= 8192 && t.net_classes <= 0x1Fu && t.rss_two_min >= 16 &&
          t.rss_two_min <= SN_MAX_SEGMENT && t.tile_stages >= 2 && t.tile_stages <= 4 && t.tile_mode >= 0 &&
          t.tile_mode <= 1;
 }
@@ -195,10 +195,16 @@ int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64
       const float t = time_of(c);
       if (t < 0.99f * best_t) best = c, best_t = t;
     }
-    for (unsigned mask = 0; mask <= 0xFu && !failed; ++mask) {
+    for (unsigned mask = 0; mask <= 0xFu && !failed; ++mask) {  // the 2..16-item classes
       sn::SegTuning c = best;
-      c.net_classes = mask;
-      if (mask == best.net_classes) continue;
+      c.net_classes = mask | (best.net_classes & 0x10u);
+      if (c.net_classes == best.net_classes) continue;
+      const float t = time_of(c);
+      if (t < 0.99f * best_t) best = c, best_t = t;
+    }
+    if (!failed) {  // 33..64 items: 64-channel warp network or Register Sample Sort
+      sn::SegTuning c = best;
+      c.net_classes = best.net_classes ^ 0x10u;
       const float t = time_of(c);
       if (t < 0.99f * best_t) best = c, best_t = t;
     }

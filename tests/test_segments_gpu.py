@@ -84,6 +84,31 @@ def test_segments_every_length(mode, dtype):
 
 
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("net64", [True, False])
+def test_segments_33_to_64(dtype, net64):
+    # segments of 33..64 items: 64-channel warp network (net_classes bit 4) or
+    # Register Sample Sort; many keys equal to the maximum (the padding value)
+    # and many ties
+    kb = np.dtype(dtype).itemsize
+    rng = np.random.default_rng(21)
+    lens = np.repeat(np.arange(33, 65, dtype=np.uint32), 40)
+    rng.shuffle(lens)
+    off = wl.offsets_from_lengths(lens)
+    total = int(off[-1])
+    k = wl.uniform_keys(total, dtype, seed=22)
+    k[rng.random(total) < 0.3] = np.iinfo(dtype).max
+    k[rng.random(total) < 0.3] = dtype(5)
+    v = np.arange(total, dtype=np.uint32)
+    try:
+        for with_vals in (True, False):
+            sn.check(sn.sn_tuning_set(kb, with_vals, net_classes=0x1F if net64 else 0xF), "set")
+            assert_parity("sn", k, v if with_vals else None, off)
+    finally:
+        for with_vals in (True, False):
+            sn.check(sn.sn_tuning_set(kb, with_vals), "defaults")
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
 def test_segments_edge_cases(dtype):
     top = np.iinfo(dtype).max
     # all-equal, max-key and empty segments, non-zero first offset

@@ -13,9 +13,9 @@ pytestmark = pytest.mark.gpu
 
 SETS = [dict(tile_units=512, net_classes=0x0, rss_two_min=16, tile_stages=2, tile_mode=0),
         dict(tile_units=4096, net_classes=0xF, rss_two_min=256, tile_stages=2, tile_mode=1),
-        dict(tile_units=1024, net_classes=0x5, rss_two_min=64, tile_stages=4, tile_mode=0),
+        dict(tile_units=1024, net_classes=0x15, rss_two_min=64, tile_stages=4, tile_mode=0),
         dict(tile_units=2048, net_classes=0xA, rss_two_min=200, tile_stages=3, tile_mode=1),
-        dict(tile_units=512, net_classes=0x4, rss_two_min=128, tile_stages=3, tile_mode=1),
+        dict(tile_units=512, net_classes=0x14, rss_two_min=128, tile_stages=3, tile_mode=1),
         dict(tile_units=1024, net_classes=0x0, rss_two_min=160, tile_stages=4, tile_mode=1)]
 
 
