@@ -123,6 +123,13 @@ __device__ __forceinline__ Item64 pick(const Item64& mine, const Item64& other, 
   const bool take = keep_min ? item_less(other, mine) : item_less(mine, other);
   return take ? other : mine;
 }
+template <class K>
+__device__ __forceinline__ KeyIdx<K> pick(const KeyIdx<K>& mine, const KeyIdx<K>& other, bool keep_min) {
+  // by key alone; on equal keys each lane keeps its own item, so a lane
+  // exchange stays a permutation
+  const bool take = keep_min ? other.k < mine.k : mine.k < other.k;
+  return take ? other : mine;
+}
 
 // -------------------------------------------------------- networks --------
 
@@ -225,6 +232,10 @@ __device__ __forceinline__ uint64_t shfl_idx(uint64_t v, int src) { return __shf
 __device__ __forceinline__ Item64 shfl_idx(const Item64& v, int src) {
   return Item64{__shfl_sync(0xFFFFFFFFu, v.key, src), __shfl_sync(0xFFFFFFFFu, v.idx, src)};
 }
+template <class K>
+__device__ __forceinline__ KeyIdx<K> shfl_idx(const KeyIdx<K>& v, int src) {
+  return KeyIdx<K>{shfl_idx(v.k, src), __shfl_sync(0xFFFFFFFFu, v.ix, src)};
+}
 
 // 32-lane warp network (generated schedule): lane l meets lane l ^ M at every
 // step; the lower lane keeps the smaller item.
@@ -233,6 +244,45 @@ __device__ __forceinline__ void warp_network32(T& x, int lane) {
 #define SN_WARP_STEP_(M) { const T o = shfl_xor(x, M); x = pick(x, o, lane < (lane ^ (M))); }
   SN_WARP32_SCHEDULE(SN_WARP_STEP_)
 #undef SN_WARP_STEP_
+}
+
+// Two independent columns through the same network, step by step, so that
+// their shuffles and compares interleave.
+template <class T>
+__device__ __forceinline__ void warp_network32x2(T& x, T& y, int lane) {
+#define SN_WARP_STEP2_(M)                        \
+  {                                              \
+    const T ox = shfl_xor(x, M);                 \
+    const T oy = shfl_xor(y, M);                 \
+    const bool keep_min = lane < (lane ^ (M));   \
+    x = pick(x, ox, keep_min);                   \
+    y = pick(y, oy, keep_min);                   \
+  }
+  SN_WARP32_SCHEDULE(SN_WARP_STEP2_)
+#undef SN_WARP_STEP2_
+}
+
+// 64 items on a warp, slot 32 r + lane in register r (lo: r = 0, hi: r = 1),
+// sorted ascending: each column by the 32-lane network; then slot l meets
+// slot 63 - l in one compare-exchange (so equal keys stay a permutation),
+// leaving the 32 smallest as a bitonic sequence in lo and the 32 largest as
+// one in hi (lane order); the half-cleaners 16, 8, 4, 2, 1 sort each.
+template <class T>
+__device__ __forceinline__ void warp_sort64(T& lo, T& hi, int lane) {
+  warp_network32x2(lo, hi, lane);
+  {
+    const T y = shfl_idx(hi, 31 - lane);
+    const bool sw = item_less(y, lo);
+    hi = sw ? lo : y;
+    lo = sw ? y : lo;
+  }
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const bool keep_min = (lane & m) == 0;
+    const T a = shfl_xor(lo, m), b = shfl_xor(hi, m);
+    lo = pick(lo, a, keep_min);
+    hi = pick(hi, b, keep_min);
+  }
 }
 
 // Comparator `c` of the step with XOR mask `mask` of the ascending bitonic

@@ -501,46 +501,59 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K, kVals>& rm, in
 }
 
 // Segments of 33..64 items outside the RSS-only calls (launch parameter
-// net_classes bit 4): a 64-channel warp network, two items per lane, in place
-// of Register Sample Sort, whose sample sort and classification cost more
-// than the whole network at this size.  Item e = 32 r + lane starts in
-// register r; the 32-lane network sorts each register column, then slot l
-// meets slot 63 - l (the smaller items form a bitonic lower half, the larger
-// a bitonic upper half in lane order) and the half-cleaners 16, 8, 4, 2, 1
-// sort each half, leaving sorted slot 32 r + lane in register r.  With a
-// payload the items are (key, position) pairs, so equal keys keep their
-// input order.
+// net_classes bit 4): a 64-channel warp network, two items per lane
+// (warp_sort64), in place of Register Sample Sort, whose sample sort and
+// classification cost more than the whole network at this size.  With a
+// payload the items carry their positions: 4-byte keys packed with them into
+// one 64-bit word (one min/max orders both), 8-byte keys ordered by key first
+// and, only when equal keys end out of position order somewhere, once more
+// by (key, position).
 template <class K, bool kVals, bool kF>
 __device__ __forceinline__ void net64_segment(const K* kbuf, const uint32_t* vbuf, int p, int pv, int L, int lane,
                                               K* __restrict__ gk, uint32_t* __restrict__ gv) {
-  using IO = RssIO<K, kVals>;
-  using It = typename IO::T;
   const int e1 = 32 + lane;
-  It lo = lane < L ? IO::make(key_enc<K, kF>(kbuf[p + lane]), static_cast<uint32_t>(lane))
-                   : IO::sentinel(static_cast<uint32_t>(lane));
-  It hi = e1 < L ? IO::make(key_enc<K, kF>(kbuf[p + e1]), static_cast<uint32_t>(e1))
-                 : IO::sentinel(static_cast<uint32_t>(e1));
-  warp_network32(lo, lane);
-  warp_network32(hi, lane);
-  {
-    const It y = shfl_idx(hi, 31 - lane);
-    hi = pick(lo, y, false);
-    lo = pick(lo, y, true);
-  }
-#pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) {
-    const bool keep_min = (lane & m) == 0;
-    const It a = shfl_xor(lo, m), b = shfl_xor(hi, m);
-    lo = pick(lo, a, keep_min);
-    hi = pick(hi, b, keep_min);
-  }
-  if (lane < L) {
-    gk[lane] = key_dec<K, kF>(IO::key(lo));
-    if constexpr (kVals) gv[lane] = vbuf[pv + IO::idx(lo)];
-  }
-  if (e1 < L) {
-    gk[e1] = key_dec<K, kF>(IO::key(hi));
-    if constexpr (kVals) gv[e1] = vbuf[pv + IO::idx(hi)];
+  constexpr K kTop = static_cast<K>(~static_cast<K>(0));
+  if constexpr (kVals && sizeof(K) == 8) {
+    KeyIdx<K> lo{lane < L ? key_enc<K, kF>(kbuf[p + lane]) : kTop, static_cast<uint32_t>(lane)};
+    KeyIdx<K> hi{e1 < L ? key_enc<K, kF>(kbuf[p + e1]) : kTop, static_cast<uint32_t>(e1)};
+    warp_sort64(lo, hi, lane);
+    // neighbouring slots: (lane - 1, lane) in each register, (31 of lo, 0 of hi)
+    const KeyIdx<K> lo_prev = shfl_idx(lo, (lane + 31) & 31);
+    const KeyIdx<K> hi_prev = shfl_idx(hi, (lane + 31) & 31);
+    const uint32_t real = static_cast<uint32_t>(L);
+    const bool tie = lane > 0 ? (tie_misordered(lo_prev, lo, real) || tie_misordered(hi_prev, hi, real))
+                              : tie_misordered(lo_prev, hi, real);
+    if (__any_sync(kFull, tie)) {
+      using FI = ItemOf<K>;
+      typename FI::T a = FI::make(lo.k, lo.ix), b = FI::make(hi.k, hi.ix);
+      warp_sort64(a, b, lane);
+      lo = KeyIdx<K>{FI::key(a), FI::idx(a)};
+      hi = KeyIdx<K>{FI::key(b), FI::idx(b)};
+    }
+    if (lane < L) {
+      gk[lane] = key_dec<K, kF>(lo.k);
+      gv[lane] = vbuf[pv + lo.ix];
+    }
+    if (e1 < L) {
+      gk[e1] = key_dec<K, kF>(hi.k);
+      gv[e1] = vbuf[pv + hi.ix];
+    }
+  } else {
+    using IO = RssIO<K, kVals>;
+    using It = typename IO::T;
+    It lo = lane < L ? IO::make(key_enc<K, kF>(kbuf[p + lane]), static_cast<uint32_t>(lane))
+                     : IO::sentinel(static_cast<uint32_t>(lane));
+    It hi = e1 < L ? IO::make(key_enc<K, kF>(kbuf[p + e1]), static_cast<uint32_t>(e1))
+                   : IO::sentinel(static_cast<uint32_t>(e1));
+    warp_sort64(lo, hi, lane);
+    if (lane < L) {
+      gk[lane] = key_dec<K, kF>(IO::key(lo));
+      if constexpr (kVals) gv[lane] = vbuf[pv + IO::idx(lo)];
+    }
+    if (e1 < L) {
+      gk[e1] = key_dec<K, kF>(IO::key(hi));
+      if constexpr (kVals) gv[e1] = vbuf[pv + IO::idx(hi)];
+    }
   }
 }
 
@@ -1432,17 +1445,33 @@ __global__ void __launch_bounds__(kRssThreads, rss_min_blocks<K, kVals>())
         s0 = tile_first[t];
       }
     }
-    // round j: lane i fetches the j-th RSS segment of its tile (one round
-    // trip per round for all 32 tiles of the chunk); the segments found are
-    // staged and sorted in lane order
-    const uint32_t rounds = __reduce_max_sync(kFull, rc);
-    for (uint32_t j = 0; j < rounds && !failed; ++j) {
+    // The chunk's RSS segments form one list (lane i's tile contributing rc_i
+    // entries after those of lanes < i); batches of 32 entries are fetched one
+    // per lane, each lane finding its entry's tile by a binary search over the
+    // inclusive scan, so one round trip finds up to 32 segments however they
+    // are spread over the tiles.  The segments found are staged and sorted in
+    // list order.
+    uint32_t incl = rc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    for (uint32_t b0 = 0; b0 < total && !failed; b0 += 32) {
+      const uint32_t k = b0 + static_cast<uint32_t>(lane);
+      int i = 0;  // lanes before the entry's tile: those with incl <= k
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1)
+        if (__shfl_sync(kFull, incl, i + step - 1) <= k) i += step;
+      const uint32_t s0i = __shfl_sync(kFull, s0, i), basei = __shfl_sync(kFull, base, i);
+      const uint32_t firsti = __shfl_sync(kFull, incl - rc, i);
       uint32_t e0q = 0, Lq = 0;
-      const bool has = j < rc;
+      const bool has = k < total;
       if (has) {
-        const uint32_t local = order[s0 + base + j];
-        e0q = offsets[s0 + local];
-        Lq = offsets[s0 + local + 1] - e0q;
+        const uint32_t local = order[s0i + basei + (k - firsti)];
+        e0q = offsets[s0i + local];
+        Lq = offsets[s0i + local + 1] - e0q;
       }
       unsigned m = __ballot_sync(kFull, has);
       while (m && !failed) {
