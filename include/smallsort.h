@@ -199,8 +199,9 @@ int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning *t);
 /*
  * Autotuner: times sn_sort_segments on the caller's batch (device pointers,
  * same contract as sn_sort_segments / _u64 with key_bytes 4 / 8) under
- * candidate parameters -- a coordinate search over tile_mode, net_classes,
- * (tile_units, tile_stages) and rss_two_min, best of three runs each, the input restored from a device
+ * candidate parameters -- a coordinate search over net_classes, (tile_units,
+ * tile_stages) and rss_two_min with tile_mode 0 (tile_mode 1 only through
+ * sn_tuning_set), best of three runs each, the input restored from a device
  * copy before every run -- installs the fastest set for this key type and
  * payload kind on the current device and copies it to `out` (may be NULL).
  * Synchronous: returns after the search; the batch is left sorted.

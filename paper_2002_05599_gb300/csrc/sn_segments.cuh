@@ -51,7 +51,7 @@ namespace sn {
 namespace seg {
 namespace {  // internal linkage: each instantiation unit gets its own copy
 
-constexpr int kTileWarps = 8;
+constexpr int kTileWarps = 15;
 constexpr int kTileConsumers = kTileWarps * 32;
 constexpr int kTileThreads = kTileConsumers + 32;  // + one producer warp
 constexpr int kMaxStages = 4;  // tile-kernel staging depth: 2..4 stages (a launch parameter)
@@ -796,12 +796,17 @@ __device__ __forceinline__ TileTasks tile_tasks(const uint16_t* cnt) {
   return t;
 }
 
-// Resident tile-kernel blocks per SM the register budget is sized for: the
-// (key, position) networks of payload sorts need about 96 registers a thread
-// (2 blocks), keys-only networks far fewer (3 blocks for u64, 4 for u32 keys),
-// and more blocks keep more tiles in flight.
+// Resident blocks per SM the register budget is sized for.  Ring kernel
+// (16 warps a block): the (key, position) networks of payload sorts need
+// about 128 registers a thread (1 block), keys-only networks 64 (2 blocks).
+// Synchronous kernel (8 warps): 2 blocks with payload, 3 (u64) or 4 (u32)
+// keys-only; more blocks keep more tiles in flight.
 template <class K, bool kVals>
 constexpr int tile_min_blocks() {
+  return kVals ? 1 : 2;
+}
+template <class K, bool kVals>
+constexpr int sync_min_blocks() {
   return kVals ? 2 : (sizeof(K) == 4 ? 4 : 3);
 }
 
@@ -1150,7 +1155,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
 }
 
 template <class K, bool kVals, int kStages, bool kF>
-__global__ void __launch_bounds__(kSyncThreads, tile_min_blocks<K, kVals>())
+__global__ void __launch_bounds__(kSyncThreads, sync_min_blocks<K, kVals>())
     seg_sync_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
                     const Plan* plan, const uint32_t* __restrict__ tile_first, uint32_t E, uint32_t net_mask,
                     bool rss_only, unsigned* status) {

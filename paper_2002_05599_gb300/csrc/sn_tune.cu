@@ -2,7 +2,8 @@
 // include/smallsort.h: sn_tuning_*, sn_tune_segments).
 //
 // The table holds one SegTuning per (device, key type, payload kind).  The
-// tuner is a coordinate search: starting from the installed set it sweeps one
+// tuner is a coordinate search: starting from the installed set (with the
+// ring tile kernel, tile_mode 0) it sweeps one
 // parameter at a time over its candidates with the others fixed (skipping
 // tile shapes whose staging does not fit in shared memory), keeps a candidate
 // only if it is more than 1% faster, and makes two passes.  Every
@@ -183,18 +184,16 @@ int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64
   };
 
   sn::SegTuning best = sn::current_tuning(d->device, key_bytes, with_vals);
+  // The search keeps the ring tile kernel (tile_mode 0): the synchronous
+  // kernel stages every tile, with tile work or not, so a batch that times
+  // well with it under sn_sort_segments can be slower under rss_sort_segments,
+  // which shares the parameter set; it stays available through sn_tuning_set.
+  best.tile_mode = 0;
   float best_t = time_of(best);
   static const int kTiles[] = {512, 1024, 2048, 4096, 8192};
   static const int kStagesC[] = {2, 3, 4};
   static const int kTwo[] = {32, 64, 96, 128, 160, 192, 224, 256};
   for (int pass = 0; pass < 2 && !failed; ++pass) {
-    for (int mode = 0; mode <= 1 && !failed; ++mode) {
-      if (mode == best.tile_mode) continue;
-      sn::SegTuning c = best;
-      c.tile_mode = mode;
-      const float t = time_of(c);
-      if (t < 0.99f * best_t) best = c, best_t = t;
-    }
     for (unsigned mask = 0; mask <= 0xFu && !failed; ++mask) {  // the 2..16-item classes
       sn::SegTuning c = best;
       c.net_classes = mask | (best.net_classes & 0x10u);
