@@ -15,7 +15,7 @@
 //    counter); a producer warp reads the metadata of 32 tiles at a time,
 //    skips tiles with nothing to do and stages the others
 //    (offsets, keys, payload, bins) in shared memory with 1-D bulk copies on
-//    a two-stage mbarrier ring, eight consumer warps take work items:
+//    a ring of 2..4 mbarrier stages, fifteen consumer warps take work items:
 //      * 2..16 items: 32 segments per item, one per lane, each sorted in
 //        registers by the network of Sec. 2 for its class (2, 4, 8, 12 or 16
 //        channels, shorter segments padded with +inf);
@@ -26,12 +26,14 @@
 //    Sorted tiles return through bulk stores; the partial 16-byte granules at
 //    a tile's ends, shared with its neighbours, are written with plain stores.
 // 4. seg_rss_kernel -- persistent independent warps, tiles assigned
-//    round-robin to warps; each warp walks the RSS entries of its tiles and
-//    prefetches its next segment with a bulk copy while it sorts the
-//    current one by Register Sample Sort (Sec. 3): a sample of 2k items sorted
-//    by a network, k-1 splitters taken equidistant, the branch-free descent
+//    round-robin to warps; each warp lists the RSS entries of its tiles,
+//    stages segments with bulk copies two ahead of the one it sorts, and sorts
+//    each by Register Sample Sort (Sec. 3): a sample of a*k items sorted by a
+//    network, k-1 splitters taken equidistant, the branch-free descent
 //    j <- 2j + [t_j < e] over the splitter tree (Algorithm 1 generalised), a
-//    stable counting scatter, and a network per bucket.
+//    counting scatter, and a network per bucket; results go straight to
+//    global memory.  Segments of 33..64 items may take a 64-channel warp
+//    network instead (a launch parameter; never in the RSS-only calls).
 // With a payload, items are (key, position) pairs so ties keep input order and
 // the payload is gathered by position at the end.  Few distinct network sizes
 // keep the instruction working set small: with one network per n, warps
@@ -175,8 +177,10 @@ struct RssWarpLayout {
 // ---------------------------------------------------------------- plan -----
 
 __global__ void __launch_bounds__(256)
-    seg_plan_kernel(const uint32_t* __restrict__ offsets, uint64_t nseg, uint32_t E, Plan* plan,
+    seg_plan_kernel(const uint32_t* __restrict__ offsets, uint64_t nseg, uint32_t E, int e_shift, Plan* plan,
                     uint32_t* __restrict__ tile_first, uint64_t tile_cap, unsigned* status) {
+  // tile of position u: u / E, a shift when E is a power of two (e_shift >= 0)
+  auto tile_of = [&](uint64_t u) -> uint64_t { return e_shift >= 0 ? u >> e_shift : u / E; };
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   const uint32_t base = offsets[0];
   bool bad = false;
@@ -185,11 +189,11 @@ __global__ void __launch_bounds__(256)
     const uint32_t o1 = offsets[s + 1];
     if (o1 < o || o1 - o > kMaxSeg || o < base) bad = true;
     const uint64_t u = s + static_cast<uint64_t>(o - base);
-    const uint64_t t = u / E;
+    const uint64_t t = tile_of(u);
     uint64_t tp = ~0ull;
     if (s > 0) {
       const uint32_t op = offsets[s - 1];
-      tp = ((s - 1) + static_cast<uint64_t>(op - base)) / E;
+      tp = tile_of((s - 1) + static_cast<uint64_t>(op - base));
     }
     if (t != tp && t < tile_cap) tile_first[t] = static_cast<uint32_t>(s);
     if (s == nseg - 1) {
@@ -211,46 +215,81 @@ __global__ void __launch_bounds__(256)
 
 // One warp per tile (grid-stride over warps): counts[8t + c] for the tile
 // classes c and counts[8t + 6] for Register Sample Sort, and the tile-local
-// indices of its segments grouped by class in order[s0 .. s1).  Counts live
-// in registers (warp-uniform); positions come from ballots.
-__global__ void __launch_bounds__(256)
+// indices of its segments grouped by class in order[s0 .. s1).  A segment's
+// class comes from a per-block table indexed by min(length, 33).  Counting:
+// each lane sets a one-byte field for its class (classes 0..3 in one word,
+// 4..7 in another) and one warp-wide add per word sums a chunk of 32
+// segments.  Placing: lanes of one class find each other with a match, and a
+// segment's position is its class's running total (per-warp shared memory)
+// plus its rank among them.  Both passes classify kBinChunks chunks of 32
+// segments at a time, so that their offset loads are in flight together.
+constexpr int kBinChunks = 4;
+constexpr int kBinWarps = 8;
+__global__ void __launch_bounds__(kBinWarps * 32)
     seg_bin_kernel(const uint32_t* __restrict__ offsets, const Plan* plan, const uint32_t* __restrict__ tile_first,
                    uint16_t* __restrict__ counts, uint16_t* __restrict__ order, bool rss_only,
                    uint32_t net_mask) {
-  constexpr int kCls = kNumTileCls + 1;  // tile classes + RSS
+  constexpr int kCls = kNumTileCls + 1;  // tile classes + RSS; kSkipCls (= kCls) is not listed
+  static_assert(kSkipCls == 7, "eight class fields");
+  __shared__ uint8_t cls_of[34];
+  __shared__ uint32_t cur_s[kBinWarps][8];
+  if (threadIdx.x < 34) cls_of[threadIdx.x] = static_cast<uint8_t>(seg_class(threadIdx.x, rss_only, net_mask));
+  __syncthreads();
   const int lane = threadIdx.x & 31;
+  uint32_t* cur = cur_s[threadIdx.x >> 5];
   const unsigned ntiles = plan->bad ? 0u : plan->ntiles;
-  const unsigned W = gridDim.x * (blockDim.x / 32);
+  const unsigned W = gridDim.x * kBinWarps;
   const unsigned lt = (1u << lane) - 1u;
-  for (unsigned t = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); t < ntiles; t += W) {
+  for (unsigned t = blockIdx.x * kBinWarps + (threadIdx.x >> 5); t < ntiles; t += W) {
     const uint32_t s0 = tile_first[t], s1 = tile_first[t + 1];
     const uint32_t ns = s1 - s0;
-    uint32_t cnt[kCls];
+    auto classify = [&](uint32_t i0, int (&c)[kBinChunks]) {
 #pragma unroll
-    for (int q = 0; q < kCls; ++q) cnt[q] = 0;
-    for (uint32_t i0 = 0; i0 < ns; i0 += 32) {
-      const uint32_t i = i0 + lane;
-      const int c = i < ns ? seg_class(offsets[s0 + i + 1] - offsets[s0 + i], rss_only, net_mask) : kSkipCls;
+      for (int u = 0; u < kBinChunks; ++u) {
+        const uint32_t i = i0 + 32u * u + lane;
+        const uint32_t len = i < ns ? offsets[s0 + i + 1] - offsets[s0 + i] : 0u;
+        c[u] = i < ns ? cls_of[len < 33u ? len : 33u] : kSkipCls;
+      }
+    };
+    // counts in 16-bit fields: acc[0] classes 0, 1; acc[1] 2, 3; acc[2] 4, 5; acc[3] 6, 7
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
+    for (uint32_t i0 = 0; i0 < ns; i0 += 32u * kBinChunks) {
+      int c[kBinChunks];
+      classify(i0, c);
 #pragma unroll
-      for (int q = 0; q < kCls; ++q) cnt[q] += __popc(__ballot_sync(kFull, c == q));
+      for (int u = 0; u < kBinChunks; ++u) {
+        const uint32_t bit = 1u << ((c[u] & 3) * 8);
+        const uint32_t a = __reduce_add_sync(kFull, c[u] < 4 ? bit : 0u);
+        const uint32_t b = __reduce_add_sync(kFull, c[u] >= 4 ? bit : 0u);
+        acc[0] += __byte_perm(a, 0u, 0x4140);
+        acc[1] += __byte_perm(a, 0u, 0x4342);
+        acc[2] += __byte_perm(b, 0u, 0x4140);
+        acc[3] += __byte_perm(b, 0u, 0x4342);
+      }
     }
-    uint32_t cur[kCls];
     uint32_t at = 0;
 #pragma unroll
-    for (int q = 0; q < kCls; ++q) {
-      cur[q] = at;
-      at += cnt[q];
-      if (lane == q) counts[8ull * t + q] = static_cast<uint16_t>(cnt[q]);
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t n = (acc[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
+      if (lane == q) {
+        cur[q] = at;
+        counts[8ull * t + q] = static_cast<uint16_t>(q < kCls ? n : 0u);
+      }
+      at += n;
     }
-    if (lane == 7) counts[8ull * t + 7] = 0;
-    for (uint32_t i0 = 0; i0 < ns; i0 += 32) {
-      const uint32_t i = i0 + lane;
-      const int c = i < ns ? seg_class(offsets[s0 + i + 1] - offsets[s0 + i], rss_only, net_mask) : kSkipCls;
+    __syncwarp();
+    for (uint32_t i0 = 0; i0 < ns; i0 += 32u * kBinChunks) {
+      int c[kBinChunks];
+      classify(i0, c);
 #pragma unroll
-      for (int q = 0; q < kCls; ++q) {
-        const unsigned m = __ballot_sync(kFull, c == q);
-        if (c == q) order[s0 + cur[q] + __popc(m & lt)] = static_cast<uint16_t>(i);
-        cur[q] += __popc(m);
+      for (int u = 0; u < kBinChunks; ++u) {
+        const uint32_t i = i0 + 32u * u + lane;
+        const unsigned m = __match_any_sync(kFull, c[u]);
+        const uint32_t below = m & lt;
+        if (c[u] < kCls) order[s0 + cur[c[u]] + __popc(below)] = static_cast<uint16_t>(i);
+        __syncwarp();
+        if (below == 0) cur[c[u]] += __popc(m);
+        __syncwarp();
       }
     }
   }
@@ -1570,11 +1609,12 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
   if (e != cudaSuccess) return e;
   const uint64_t want = (nseg + 255) / 256;
   const unsigned g1 = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(want, 16ull * d.sm_count)));
-  seg_plan_kernel<<<g1, 256, 0, stream>>>(offsets, nseg, E, plan, tile_first, sl.cap, d.status);
+  const int e_shift = (E & (E - 1)) == 0 ? __builtin_ctz(E) : -1;
+  seg_plan_kernel<<<g1, 256, 0, stream>>>(offsets, nseg, E, e_shift, plan, tile_first, sl.cap, d.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const unsigned g2 = static_cast<unsigned>(std::max<uint64_t>(
       1, std::min<uint64_t>(sl.cap - 1, 8ull * d.sm_count)));
-  seg_bin_kernel<<<g2, 256, 0, stream>>>(offsets, plan, tile_first, counts, order, rss_only,
+  seg_bin_kernel<<<g2, kBinWarps * 32, 0, stream>>>(offsets, plan, tile_first, counts, order, rss_only,
                                           tun.net_classes);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
