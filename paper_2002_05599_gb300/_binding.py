@@ -233,7 +233,7 @@ def sn_tuning_get(key_bytes: int, with_vals: bool) -> dict:
     return t.as_dict()
 
 
-def sn_tuning_set(key_bytes: int, with_vals: bool, tile_units: int = 2048, net_classes: int = 0x1F,
+def sn_tuning_set(key_bytes: int, with_vals: bool, tile_units: int = 4096, net_classes: int = 0x1F,
                   rss_two_min: int = 160, tile_stages: int = 2, tile_mode: int = 0) -> int:
     t = SnTuning(tile_units, net_classes, rss_two_min, tile_stages, tile_mode)
     return _tune_lib().sn_tuning_set(key_bytes, int(with_vals), ctypes.byref(t))

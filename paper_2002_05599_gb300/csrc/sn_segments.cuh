@@ -184,24 +184,37 @@ __global__ void __launch_bounds__(256)
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   const uint32_t base = offsets[0];
   bool bad = false;
-  for (uint64_t s = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < nseg; s += stride) {
-    const uint32_t o = offsets[s];
-    const uint32_t o1 = offsets[s + 1];
-    if (o1 < o || o1 - o > kMaxSeg || o < base) bad = true;
-    const uint64_t u = s + static_cast<uint64_t>(o - base);
-    const uint64_t t = tile_of(u);
-    uint64_t tp = ~0ull;
-    if (s > 0) {
-      const uint32_t op = offsets[s - 1];
-      tp = tile_of((s - 1) + static_cast<uint64_t>(op - base));
+  // kPlanU segments per thread and step (s, s + stride, ...), their offset
+  // loads issued together
+  constexpr int kPlanU = 4;
+  for (uint64_t sb = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; sb < nseg;
+       sb += kPlanU * stride) {
+    uint32_t o[kPlanU], o1[kPlanU], op[kPlanU];
+#pragma unroll
+    for (int u = 0; u < kPlanU; ++u) {
+      const uint64_t s = sb + u * stride;
+      o[u] = o1[u] = op[u] = 0;
+      if (s < nseg) {
+        o[u] = offsets[s];
+        o1[u] = offsets[s + 1];
+        if (s > 0) op[u] = offsets[s - 1];
+      }
     }
-    if (t != tp && t < tile_cap) tile_first[t] = static_cast<uint32_t>(s);
-    if (s == nseg - 1) {
-      if (t + 1 < tile_cap) {
-        tile_first[t + 1] = static_cast<uint32_t>(nseg);
-        plan->ntiles = static_cast<unsigned>(t + 1);
-      } else {
-        bad = true;
+#pragma unroll
+    for (int u = 0; u < kPlanU; ++u) {
+      const uint64_t s = sb + u * stride;
+      if (s >= nseg) break;
+      if (o1[u] < o[u] || o1[u] - o[u] > kMaxSeg || o[u] < base) bad = true;
+      const uint64_t t = tile_of(s + static_cast<uint64_t>(o[u] - base));
+      const uint64_t tp = s > 0 ? tile_of((s - 1) + static_cast<uint64_t>(op[u] - base)) : ~0ull;
+      if (t != tp && t < tile_cap) tile_first[t] = static_cast<uint32_t>(s);
+      if (s == nseg - 1) {
+        if (t + 1 < tile_cap) {
+          tile_first[t + 1] = static_cast<uint32_t>(nseg);
+          plan->ntiles = static_cast<unsigned>(t + 1);
+        } else {
+          bad = true;
+        }
       }
     }
   }
