@@ -193,8 +193,11 @@ typedef struct {
 /* Current parameters of the current device for (key_bytes = 4 or 8, with_vals = 0 or 1). */
 int sn_tuning_get(int key_bytes, int with_vals, sn_tuning *out);
 /* Installs parameters (SN_EINVAL if out of range, or if tile_stages tiles of
-   tile_units do not fit in shared memory for this key type and payload kind:
-   two 8192-unit stages fit only for u32 keys without payload). */
+   tile_units do not fit in shared memory for this key type, payload kind and
+   tile_mode: the ring kernel packs each stage into max(6, key + payload bytes)
+   per unit of tile_units + 256, e.g. at most two 8192-unit or four 4096-unit
+   stages for u64 keys with payload; the synchronous kernel's fixed regions take
+   more: two 8192-unit stages fit only for u32 keys without payload). */
 int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning *t);
 /*
  * Autotuner: times sn_sort_segments on the caller's batch (device pointers,

@@ -50,11 +50,12 @@ SegTuning current_tuning(int device, int key_bytes, bool vals);
 bool tuning_valid(const SegTuning& t);
 
 // Whether the tile kernel's staging (tile_units, tile_stages) fits in shared
-// memory for this key type and payload kind (sn_segments_*.cu).
-bool tile_fits_u32(bool vals, int tile_units, int stages);
-bool tile_fits_u64(bool vals, int tile_units, int stages);
-inline bool tile_fits(int key_bytes, bool vals, int tile_units, int stages) {
-  return key_bytes == 8 ? tile_fits_u64(vals, tile_units, stages) : tile_fits_u32(vals, tile_units, stages);
+// memory for this key type, payload kind and tile_mode (sn_segments_*.cu).
+bool tile_fits_u32(bool vals, int tile_units, int stages, int mode);
+bool tile_fits_u64(bool vals, int tile_units, int stages, int mode);
+inline bool tile_fits(int key_bytes, bool vals, int tile_units, int stages, int mode) {
+  return key_bytes == 8 ? tile_fits_u64(vals, tile_units, stages, mode)
+                        : tile_fits_u32(vals, tile_units, stages, mode);
 }
 
 // Device scratch needed for a segmented call with nseg segments.

@@ -91,6 +91,10 @@ struct TileMeta {
   uint32_t key_shift;     // index of keys[e0] in the staged keys
   uint32_t val_shift;     // index of vals[e0] in the staged payload
   uint32_t ord_shift;     // index of order[s0] in the staged bins
+  // ring tile kernel: byte offsets of the packed regions in the stage (the
+  // offsets start at 0) and the staged key / payload capacities in elements
+  uint32_t ord_at, cnt_at, key_at, val_at;
+  uint32_t key_cap, val_cap;
 };
 
 // ------------------------------------------------------ staging layouts ----
@@ -109,6 +113,24 @@ struct TileLayout {
     ord_at = align16(val_at + (kVals ? (E + kMaxSeg + 8) * 4 : 0));
     cnt_at = align16(ord_at + (E + 16) * 2);
     stage_bytes = align128(cnt_at + 16);
+  }
+};
+
+// Ring tile kernel staging: a staged tile's regions (offsets, bins, class
+// counts, keys, payload) are packed one after the other, each sized by the
+// tile itself (TileMeta records where they start).  A tile of ns segments and
+// `items` items has ns + items <= E + 256, so a stage of
+// max(6, key + payload bytes) bytes per unit of E + 256, plus the granule
+// rounding of each copy, holds any tile: about two thirds of the fixed
+// layout's stage for 8-byte keys with payload.
+template <class K, bool kVals>
+struct RingLayout {
+  static constexpr size_t kPerItem = sizeof(K) + (kVals ? 4 : 0);
+  static constexpr size_t kPerUnit = kPerItem > 6 ? kPerItem : 6;
+  size_t stage_bytes;
+  __host__ __device__ size_t total(int stages) const { return stages * stage_bytes; }
+  __host__ __device__ explicit RingLayout(uint32_t E) {
+    stage_bytes = align128(kPerUnit * (static_cast<size_t>(E) + kMaxSeg) + 256);
   }
 };
 
@@ -825,7 +847,9 @@ __device__ __forceinline__ void store_range(T* dst, const T* staged, uint32_t sh
 
 // ----------------------------------------------------------- tile kernel ---
 
-constexpr int kRing = 256;  // task ring slots (>= 2 tiles of tasks + sentinels)
+// Task ring slots: at least the work items of kMaxStages staged tiles plus
+// one stop item per consumer warp (tile_fits checks the tile shape against it).
+constexpr int kRing = 512;
 constexpr uint32_t kRingDone = 0xFFFFFFFFu;
 
 struct TileTasks {
@@ -867,7 +891,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
     seg_tile_kernel(K* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ offsets,
                     const Plan* plan, const uint32_t* __restrict__ tile_first, const uint16_t* __restrict__ counts,
                     const uint16_t* __restrict__ order, uint32_t E, unsigned* status) {
-  const TileLayout<K, kVals> lay(E);
+  const RingLayout<K, kVals> lay(E);
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
@@ -965,37 +989,43 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
           m.off_shift = static_cast<uint32_t>((ob + 4ull * s0j - oa) / 4);
           m.ord_shift = static_cast<uint32_t>((rb + 2ull * s0j - ra) / 2);
           m.key_shift = static_cast<uint32_t>((kb + sizeof(K) * e0j - ka) / sizeof(K));
-          uint32_t bytes = static_cast<uint32_t>((oz - oa) + (rz - ra) + 16);
           const bool has_items = e1j > e0j;
-          if (has_items) bytes += static_cast<uint32_t>(kz - ka);
           uintptr_t va = 0, vz = 0;
           if constexpr (kVals) {
             va = (vb + 4ull * e0j) & ~uintptr_t(15);
             vz = (vb + 4ull * e1j + 15) & ~uintptr_t(15);
             m.val_shift = static_cast<uint32_t>((vb + 4ull * e0j - va) / 4);
-            if (has_items) bytes += static_cast<uint32_t>(vz - va);
           } else {
             m.val_shift = 0;
           }
-          // self-check of every copy's range against its staging buffer
+          // packed regions: offsets at 0, then bins, counts, keys, payload
+          // (every size a multiple of 16, so every region starts aligned)
+          const size_t off_bytes = oz - oa, ord_bytes = rz - ra;
+          const size_t key_bytes = has_items ? kz - ka : 0, val_bytes = kVals && has_items ? vz - va : 0;
+          const size_t ord_at = off_bytes, cnt_at = ord_at + ord_bytes, key_at = cnt_at + 16;
+          const size_t val_at = key_at + key_bytes, end = val_at + val_bytes;
+          // self-check of every copy's range against the stage
           const bool args_ok = s1j > s0j && s1j - s0j <= E && e1j >= e0j && e1j - e0j <= E + kMaxSeg &&
-                               (oz - oa) <= lay.key_at - lay.off_at && (rz - ra) <= lay.cnt_at - lay.ord_at &&
-                               (!has_items || (kz - ka) <= lay.val_at - lay.key_at) &&
-                               (!kVals || !has_items || (vz - va) <= lay.ord_at - lay.val_at) &&
+                               end <= lay.stage_bytes &&
                                ((reinterpret_cast<uintptr_t>(counts) + 16ull * tj) & 15) == 0;
           if (!args_ok) {
             atomicOr(status, kStatusInternal | kCheckCopyArgs);
             staged = false;  // skip the tile; its data stays untouched
           } else {
-          mbar_arrive_expect_tx(&full[s], bytes);
-          bulk_g2s(stage + lay.off_at, reinterpret_cast<const void*>(oa), static_cast<uint32_t>(oz - oa), &full[s]);
-          bulk_g2s(stage + lay.ord_at, reinterpret_cast<const void*>(ra), static_cast<uint32_t>(rz - ra), &full[s]);
-          bulk_g2s(stage + lay.cnt_at, counts + 8ull * tj, 16, &full[s]);
+          m.ord_at = static_cast<uint32_t>(ord_at);
+          m.cnt_at = static_cast<uint32_t>(cnt_at);
+          m.key_at = static_cast<uint32_t>(key_at);
+          m.val_at = static_cast<uint32_t>(val_at);
+          m.key_cap = static_cast<uint32_t>(key_bytes / sizeof(K));
+          m.val_cap = kVals ? static_cast<uint32_t>(val_bytes / 4) : 0xFFFFFFFFu;
+          mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(end));
+          bulk_g2s(stage, reinterpret_cast<const void*>(oa), static_cast<uint32_t>(off_bytes), &full[s]);
+          bulk_g2s(stage + ord_at, reinterpret_cast<const void*>(ra), static_cast<uint32_t>(ord_bytes), &full[s]);
+          bulk_g2s(stage + cnt_at, counts + 8ull * tj, 16, &full[s]);
           if (has_items) {
-            bulk_g2s(stage + lay.key_at, reinterpret_cast<const void*>(ka), static_cast<uint32_t>(kz - ka),
-                     &full[s]);
+            bulk_g2s(stage + key_at, reinterpret_cast<const void*>(ka), static_cast<uint32_t>(key_bytes), &full[s]);
             if constexpr (kVals)
-              bulk_g2s(stage + lay.val_at, reinterpret_cast<const void*>(va), static_cast<uint32_t>(vz - va),
+              bulk_g2s(stage + val_at, reinterpret_cast<const void*>(va), static_cast<uint32_t>(val_bytes),
                        &full[s]);
           }
           }
@@ -1014,7 +1044,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
         // staged counts; the task count is broadcast
         uint32_t ntasks = 0;
         if (lane == 0)
-          ntasks = tile_tasks(reinterpret_cast<const uint16_t*>(smem + s * lay.stage_bytes + lay.cnt_at)).ntasks;
+          ntasks = tile_tasks(reinterpret_cast<const uint16_t*>(smem + s * lay.stage_bytes + meta[s].cnt_at)).ntasks;
         ntasks = __shfl_sync(kFull, ntasks, 0);
         const TileTasks tt{0, 0, ntasks, 0, 0, 0, 0, 0};
         // item = stage << 17 | phase parity of this use of the stage << 16 | index
@@ -1090,11 +1120,11 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
     }
     const TileMeta m = meta[s];  // copy: checked against the stage again before the store
     unsigned char* stage = smem + s * lay.stage_bytes;
-    const uint32_t* obuf = reinterpret_cast<const uint32_t*>(stage + lay.off_at) + m.off_shift;
-    const uint16_t* ord = reinterpret_cast<const uint16_t*>(stage + lay.ord_at) + m.ord_shift;
-    K* kbuf = reinterpret_cast<K*>(stage + lay.key_at);
-    uint32_t* vbuf = reinterpret_cast<uint32_t*>(stage + lay.val_at);
-    const TileTasks tt = tile_tasks(reinterpret_cast<const uint16_t*>(stage + lay.cnt_at));
+    const uint32_t* obuf = reinterpret_cast<const uint32_t*>(stage) + m.off_shift;
+    const uint16_t* ord = reinterpret_cast<const uint16_t*>(stage + m.ord_at) + m.ord_shift;
+    K* kbuf = reinterpret_cast<K*>(stage + m.key_at);
+    uint32_t* vbuf = reinterpret_cast<uint32_t*>(stage + m.val_at);
+    const TileTasks tt = tile_tasks(reinterpret_cast<const uint16_t*>(stage + m.cnt_at));
     const uint32_t e0 = m.e0, key_shift = m.key_shift, val_shift = m.val_shift;
     const uint32_t ns = m.s1 - m.s0;
     if (task >= tt.ntasks || tt.b2 > ns || ns > E) {
@@ -1103,8 +1133,8 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
     }
 
     // self-check: a segment's staged span must lie inside the stage buffers
-    const uint32_t key_cap = static_cast<uint32_t>((lay.val_at - lay.key_at) / sizeof(K));
-    const uint32_t val_cap = kVals ? static_cast<uint32_t>((lay.ord_at - lay.val_at) / 4) : 0xFFFFFFFFu;
+    const uint32_t key_cap = m.key_cap;
+    const uint32_t val_cap = m.val_cap;
     auto span_ok = [&](uint32_t i, uint32_t& o, uint32_t& L) -> bool {
       if (i >= ns) return false;
       o = obuf[i];
@@ -1562,16 +1592,18 @@ __global__ void __launch_bounds__(kRssThreads, rss_min_blocks<K, kVals>())
 // ------------------------------------------------------------ host side ----
 
 constexpr int kCacheDevices = 64;
-constexpr int kCacheTileSizes = 5;  // tile_units 512, 1024, ..., 8192 (powers of two); others are not cached
+constexpr int kCacheTileSizes = 7;  // tile_units 512, 1024, 2048, 3072, 4096, 6144, 8192; others are not cached
 
 // Cache entry of a launch shape for device d, tile size E and staging depth
 // (null: do not cache).
 inline std::atomic<int>* cache_slot(std::atomic<int>* cache, const DeviceInfo& d, uint32_t E, int stages) {
   int t = 0;
   if (E) {
-    if (E & (E - 1)) return nullptr;
-    t = 31 - __builtin_clz(E) - 9;
-    if (t < 0 || t >= kCacheTileSizes) return nullptr;
+    static const uint32_t kSizes[kCacheTileSizes] = {512, 1024, 2048, 3072, 4096, 6144, 8192};
+    t = -1;
+    for (int q = 0; q < kCacheTileSizes; ++q)
+      if (kSizes[q] == E) t = q;
+    if (t < 0) return nullptr;
   }
   if (d.device < 0 || d.device >= kCacheDevices || stages < 1 || stages > kMaxStages) return nullptr;
   return &cache[(d.device * kCacheTileSizes + t) * kMaxStages + (stages - 1)];
@@ -1581,11 +1613,19 @@ inline std::atomic<int>* cache_slot(std::atomic<int>* cache, const DeviceInfo& d
 // limit less a margin for the kernel's static shared memory).
 constexpr size_t kTileSmemLimit = 232448 - 4096;
 
-// Whether `stages` stages of E-unit tiles fit in a block's shared memory.
+// Whether `stages` stages of E-unit tiles fit in a block's shared memory:
+// packed stages for the ring kernel (mode 0), fixed ones for the synchronous
+// kernel (mode 1).
 template <class K, bool kVals>
-bool tile_fits(int E, int stages) {
-  return E >= 512 && E <= 8192 && stages >= 2 && stages <= kMaxStages &&
-         TileLayout<K, kVals>(static_cast<uint32_t>(E)).total(stages) <= kTileSmemLimit;
+bool tile_fits(int E, int stages, int mode) {
+  if (E < 512 || E > 8192 || stages < 2 || stages > kMaxStages) return false;
+  const uint32_t e = static_cast<uint32_t>(E);
+  const size_t bytes = mode == 1 ? TileLayout<K, kVals>(e).total(stages) : RingLayout<K, kVals>(e).total(stages);
+  // work items of one tile: a network item holds 32 segments of >= 3 units
+  // (offset + 2 items), a pair item 16 of >= 18 units; the network list is
+  // one run (a chunk may span two classes), so at most (E + 256) / 96 + 2
+  const int items_per_tile = (E + kMaxSeg) / 96 + 2;
+  return bytes <= kTileSmemLimit && stages * items_per_tile + kTileWarps <= kRing;
 }
 
 // Resident blocks per SM of `kern` with `smem` bytes of dynamic shared
@@ -1648,7 +1688,7 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
                                                    rss_only, d.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else {
-    const TileLayout<K, kVals> lay(E);
+    const RingLayout<K, kVals> lay(E);
     const int smem_bytes = static_cast<int>(lay.total(tun.tile_stages));
     auto kern = tun.tile_stages == 2   ? seg_tile_kernel<K, kVals, 2, kF>
                 : tun.tile_stages == 3 ? seg_tile_kernel<K, kVals, 3, kF>
@@ -1691,7 +1731,8 @@ cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, ui
   if (t.tile_units < 512 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg || t.net_classes > 0x1Fu ||
       t.tile_mode < 0 || t.tile_mode > 1)
     return cudaErrorInvalidValue;
-  if (!(vals ? tile_fits<K, true>(t.tile_units, t.tile_stages) : tile_fits<K, false>(t.tile_units, t.tile_stages)))
+  if (!(vals ? tile_fits<K, true>(t.tile_units, t.tile_stages, t.tile_mode)
+             : tile_fits<K, false>(t.tile_units, t.tile_stages, t.tile_mode)))
     return cudaErrorInvalidValue;
   if (scratch_bytes < ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total) return cudaErrorInvalidValue;
   const bool rss = mode == SegMode::kRssOnly;

@@ -9,8 +9,9 @@ cudaError_t launch_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* 
   return seg::launch_segments<uint64_t>(keys, vals, offsets, nseg, mode, scratch, scratch_bytes, t, s, d);
 }
 
-bool tile_fits_u64(bool vals, int tile_units, int stages) {
-  return vals ? seg::tile_fits<uint64_t, true>(tile_units, stages) : seg::tile_fits<uint64_t, false>(tile_units, stages);
+bool tile_fits_u64(bool vals, int tile_units, int stages, int mode) {
+  return vals ? seg::tile_fits<uint64_t, true>(tile_units, stages, mode)
+              : seg::tile_fits<uint64_t, false>(tile_units, stages, mode);
 }
 
 }  // namespace sn

@@ -104,7 +104,7 @@ int sn_tuning_get(int key_bytes, int with_vals, sn_tuning* out) {
 int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning* t) {
   if (t == nullptr || (key_bytes != 4 && key_bytes != 8)) return SN_EINVAL;
   const sn::SegTuning st = sn::from_c(*t);
-  if (!sn::tuning_valid(st) || !sn::tile_fits(key_bytes, with_vals != 0, st.tile_units, st.tile_stages))
+  if (!sn::tuning_valid(st) || !sn::tile_fits(key_bytes, with_vals != 0, st.tile_units, st.tile_stages, st.tile_mode))
     return SN_EINVAL;
   int err = SN_OK;
   const sn::DeviceInfo* d = sn::device_info(&err);
@@ -190,7 +190,7 @@ int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64
   // which shares the parameter set; it stays available through sn_tuning_set.
   best.tile_mode = 0;
   float best_t = time_of(best);
-  static const int kTiles[] = {512, 1024, 2048, 4096, 8192};
+  static const int kTiles[] = {512, 1024, 2048, 3072, 4096, 6144, 8192};
   static const int kStagesC[] = {2, 3, 4};
   static const int kTwo[] = {32, 64, 96, 128, 160, 192, 224, 256};
   for (int pass = 0; pass < 2 && !failed; ++pass) {
@@ -210,7 +210,7 @@ int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64
     for (int tu : kTiles) {
       for (int st : kStagesC) {
         if (failed || (tu == best.tile_units && st == best.tile_stages) ||
-            !sn::tile_fits(key_bytes, with_vals, tu, st))
+            !sn::tile_fits(key_bytes, with_vals, tu, st, best.tile_mode))
           continue;
         sn::SegTuning c = best;
         c.tile_units = tu;
@@ -285,7 +285,7 @@ int sn_tuning_load(const char* path) {
     t.tile_stages = st;
     t.tile_mode = mode;
     if (dev < 0 || dev >= sn::kDevs || (kb != 4 && kb != 8) || (v != 0 && v != 1) || !sn::tuning_valid(t) ||
-        !sn::tile_fits(kb, v != 0, t.tile_units, t.tile_stages)) {
+        !sn::tile_fits(kb, v != 0, t.tile_units, t.tile_stages, t.tile_mode)) {
       rc = SN_EINVAL;
       break;
     }

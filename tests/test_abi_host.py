@@ -125,7 +125,7 @@ def test_tuning_argument_errors_and_file_format(lib, tmp_path):
     for bad in (SnTuning(256, 0xF, 160, 2, 0), SnTuning(16384, 0xF, 160, 2, 0), SnTuning(2048, 0x20, 160, 2, 0),
                 SnTuning(2048, 0xF, 8, 2, 0), SnTuning(2048, 0xF, 300, 2, 0), SnTuning(2048, 0xF, 160, 1, 0),
                 SnTuning(2048, 0xF, 160, 5, 0), SnTuning(2048, 0xF, 160, 2, 2),
-                SnTuning(8192, 0xF, 160, 2, 0)):  # last: staging too large
+                SnTuning(8192, 0xF, 160, 4, 0), SnTuning(8192, 0xF, 160, 2, 1)):  # last two: staging too large
         assert L.sn_tuning_set(4, 1, ctypes.byref(bad)) == -1
     L.sn_tune_segments.argtypes = L.sn_tune_segments.argtypes
     assert L.sn_tune_segments(None, None, None, 5, 4, None, None, None) == -1
@@ -139,7 +139,7 @@ def test_tuning_argument_errors_and_file_format(lib, tmp_path):
         f.write("smallsort-tuning 3\n0 4 0 100 15 160 2 0\n")  # tile size out of range
     assert sn.sn_tuning_load(bad_file) == -1
     with open(bad_file, "w") as f:
-        f.write("smallsort-tuning 3\n0 8 1 4096 15 160 4 0\n")  # four 4096-unit stages do not fit
+        f.write("smallsort-tuning 3\n0 8 1 8192 15 160 3 0\n")  # three 8192-unit stages do not fit
     assert sn.sn_tuning_load(bad_file) == -1
     with open(bad_file, "w") as f:
         f.write("smallsort-tuning 2\n0 4 0 2048 15 160 2\n")  # old format

@@ -49,19 +49,34 @@ def test_every_parameter_set_gives_the_same_result(dtype, with_vals, restore_def
 
 
 def test_tile_size_limit_by_shared_memory(restore_defaults):
-    # two stages of 8192-unit tiles fit in shared memory only for u32 keys without payload
-    assert sn.sn_tuning_set(4, False, tile_units=8192) == sn.SN_OK
+    # ring kernel (packed stages): a stage takes max(6, key + payload bytes) per
+    # unit of tile_units + 256, and a block at most 223 KB
+    assert sn.sn_tuning_set(4, False, tile_units=8192, tile_stages=4) == sn.SN_OK   # 6 B per unit
+    for kb, v in ((4, True), (8, False)):                                           # 8 B per unit
+        assert sn.sn_tuning_set(kb, v, tile_units=8192, tile_stages=3) == sn.SN_OK
+        assert sn.sn_tuning_set(kb, v, tile_units=8192, tile_stages=4) == sn.SN_EINVAL
+    assert sn.sn_tuning_set(8, True, tile_units=8192, tile_stages=2) == sn.SN_OK    # 12 B per unit
+    assert sn.sn_tuning_set(8, True, tile_units=8192, tile_stages=3) == sn.SN_EINVAL
+    assert sn.sn_tuning_set(8, True, tile_units=4096, tile_stages=4) == sn.SN_OK
+    # synchronous kernel (fixed regions): two 8192-unit stages only for u32 keys alone
+    assert sn.sn_tuning_set(4, False, tile_units=8192, tile_mode=1) == sn.SN_OK
     for kb, v in ((4, True), (8, False), (8, True)):
-        assert sn.sn_tuning_set(kb, v, tile_units=8192) == sn.SN_EINVAL
-        assert sn.sn_tuning_set(kb, v, tile_units=4096) == sn.SN_OK
-        assert sn.sn_tuning_set(kb, v, tile_units=4096, tile_stages=4) == sn.SN_EINVAL
-        assert sn.sn_tuning_set(kb, v, tile_units=2048, tile_stages=4) == sn.SN_OK
+        assert sn.sn_tuning_set(kb, v, tile_units=8192, tile_mode=1) == sn.SN_EINVAL
+    # the largest shapes sort correctly
     k, _, off = wl.segment_batch(50_000, "geometric", "uniform", np.uint32, False, seed=79, p=0.15, cap=256)
     dk = to_dev(k)
-    sn.check(sn.sn_tuning_set(4, False, tile_units=8192), "set")
+    sn.check(sn.sn_tuning_set(4, False, tile_units=8192, tile_stages=4), "set")
     sn.check(sn.sn_sort_segments(dk, None, to_dev(off)), "sort")
     assert sn.sn_check() == sn.SN_OK
     assert np.array_equal(to_host(dk, np.uint32), oracle.sort_segments(k, None, off)[0])
+    k, v, off = wl.segment_batch(60_000, "geometric", "fewdistinct", np.uint64, True, seed=80, p=0.15, cap=256)
+    ek, ev = oracle.sort_segments(k, v, off)
+    for units, stages in ((8192, 2), (6144, 2), (4096, 4), (3072, 3)):
+        dk, dv = to_dev(k), to_dev(v)
+        sn.check(sn.sn_tuning_set(8, True, tile_units=units, tile_stages=stages), "set")
+        sn.check(sn.sn_sort_segments_u64(dk, dv, to_dev(off)), "sort")
+        assert sn.sn_check() == sn.SN_OK
+        assert np.array_equal(to_host(dk, np.uint64), ek) and np.array_equal(to_host(dv, np.uint32), ev), units
 
 
 def test_autotuner_installs_its_choice_and_sorts(tmp_path, restore_defaults):
