@@ -298,10 +298,11 @@ def bench_ours(args, rank, world, local_rank, dist):
     sn.check(status, "warm-up")
     tuned = {}
     if not args.no_tune:  # autotune each segmented workload on its own batch (untimed)
+        restore()  # on unsorted input: the warm-up left the batches sorted
         if "uneven" in parts:
             tuned["uneven"] = autotune(sn, work["uneven_keys"], work["uneven_vals"], work["uneven_off"])
         if "rss" in parts:
-            tuned["rss"] = autotune(sn, work["rss_keys"], None, work["rss_off"])
+            tuned["rss"] = autotune(sn, work["rss_keys"], None, work["rss_off"], rss_only=True)
     graphs = {}
     if "uneven" in parts and not args.no_graph:
         graphs["uneven"] = capture_uneven(sn, work)
@@ -408,9 +409,10 @@ def bench_ours(args, rank, world, local_rank, dist):
     return result
 
 
-def autotune(sn, keys, vals, offsets):
-    """sn_tune_segments on a batch; returns the installed parameters and the tuned time."""
-    params, ms = sn.sn_tune_segments(keys, vals, offsets)
+def autotune(sn, keys, vals, offsets, rss_only=False):
+    """sn_tune_segments (sn_tune_rss_segments if rss_only) on a batch; returns
+    the installed parameters and the tuned time."""
+    params, ms = sn.sn_tune_segments(keys, vals, offsets, rss_only=rss_only)
     return dict(params, tuned_ms=round(ms, 4))
 
 

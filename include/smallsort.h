@@ -213,6 +213,10 @@ int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning *t);
  */
 int sn_tune_segments(void *keys, uint32_t *vals, const uint32_t *offsets, uint64_t nseg, int key_bytes,
                      sn_stream_t stream, sn_tuning *out, float *best_ms);
+/* The same search timing rss_sort_segments / rss_sort_segments_u64 instead
+   (same arguments, same parameter table). */
+int sn_tune_rss_segments(void *keys, uint32_t *vals, const uint32_t *offsets, uint64_t nseg, int key_bytes,
+                         sn_stream_t stream, sn_tuning *out, float *best_ms);
 /*
  * Writes every parameter set that was set or tuned in this process to a text
  * file (one line per device, key type and payload kind), and reads such a file

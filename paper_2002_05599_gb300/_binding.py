@@ -217,11 +217,13 @@ def _tune_lib():
         P = ctypes.c_void_p
         lib.sn_tuning_get.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SnTuning)]
         lib.sn_tuning_set.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(SnTuning)]
-        lib.sn_tune_segments.argtypes = [P, P, P, ctypes.c_uint64, ctypes.c_int, P, ctypes.POINTER(SnTuning),
-                                         ctypes.POINTER(ctypes.c_float)]
+        for name in ("sn_tune_segments", "sn_tune_rss_segments"):
+            getattr(lib, name).argtypes = [P, P, P, ctypes.c_uint64, ctypes.c_int, P, ctypes.POINTER(SnTuning),
+                                           ctypes.POINTER(ctypes.c_float)]
         lib.sn_tuning_save.argtypes = [ctypes.c_char_p]
         lib.sn_tuning_load.argtypes = [ctypes.c_char_p]
-        for name in ("sn_tuning_get", "sn_tuning_set", "sn_tune_segments", "sn_tuning_save", "sn_tuning_load"):
+        for name in ("sn_tuning_get", "sn_tuning_set", "sn_tune_segments", "sn_tune_rss_segments", "sn_tuning_save",
+                     "sn_tuning_load"):
             getattr(lib, name).restype = ctypes.c_int
         lib._tune_bound = True
     return lib
@@ -239,14 +241,16 @@ def sn_tuning_set(key_bytes: int, with_vals: bool, tile_units: int = 4096, net_c
     return _tune_lib().sn_tuning_set(key_bytes, int(with_vals), ctypes.byref(t))
 
 
-def sn_tune_segments(keys, vals, offsets, nseg: int | None = None, stream=None):
-    """Autotune the segmented call on this batch; returns (parameters, ms of one sort)."""
+def sn_tune_segments(keys, vals, offsets, nseg: int | None = None, stream=None, rss_only: bool = False):
+    """Autotune the segmented call (rss_sort_segments* if rss_only) on this
+    batch; returns (parameters, ms of one sort)."""
     if nseg is None:
         nseg = _elems(offsets, 4) - 1
     kb = keys.element_size()
     t, ms = SnTuning(), ctypes.c_float()
-    check(_tune_lib().sn_tune_segments(_addr(keys), _addr(vals), _addr(offsets), nseg, kb, _stream(stream),
-                                       ctypes.byref(t), ctypes.byref(ms)), "sn_tune_segments")
+    name = "sn_tune_rss_segments" if rss_only else "sn_tune_segments"
+    check(getattr(_tune_lib(), name)(_addr(keys), _addr(vals), _addr(offsets), nseg, kb, _stream(stream),
+                                     ctypes.byref(t), ctypes.byref(ms)), name)
     return t.as_dict(), float(ms.value)
 
 

@@ -113,8 +113,14 @@ int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning* t) {
   return SN_OK;
 }
 
-int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, int key_bytes,
-                     sn_stream_t stream, sn_tuning* out, float* best_ms) {
+}  // extern "C"
+
+namespace {
+
+// The search of sn_tune_segments / sn_tune_rss_segments: `mode` is the call
+// whose time is minimised (the two calls share the parameter table).
+int tune(void* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, int key_bytes, sn_stream_t stream,
+         sn_tuning* out, float* best_ms, sn::SegMode mode) {
   if (key_bytes != 4 && key_bytes != 8) return SN_EINVAL;
   if (nseg == 0 || keys == nullptr || offsets == nullptr) return SN_EINVAL;
   if (nseg >= (1ull << 32)) return SN_ERANGE;
@@ -162,10 +168,10 @@ int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64
   };
   auto run = [&](const sn::SegTuning& t) -> cudaError_t {
     return key_bytes == 4
-               ? sn::launch_segments_u32(static_cast<uint32_t*>(keys), vals, offsets, nseg,
-                                         sn::SegMode::kNetworkWarpRss, scratch.p, scratch_b, t, s, *d)
-               : sn::launch_segments_u64(static_cast<uint64_t*>(keys), vals, offsets, nseg,
-                                         sn::SegMode::kNetworkWarpRss, scratch.p, scratch_b, t, s, *d);
+               ? sn::launch_segments_u32(static_cast<uint32_t*>(keys), vals, offsets, nseg, mode, scratch.p,
+                                         scratch_b, t, s, *d)
+               : sn::launch_segments_u64(static_cast<uint64_t*>(keys), vals, offsets, nseg, mode, scratch.p,
+                                         scratch_b, t, s, *d);
   };
   bool failed = false;
   auto time_of = [&](const sn::SegTuning& t) -> float {
@@ -238,6 +244,20 @@ int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64
   if (out) *out = sn::to_c(best);
   if (best_ms) *best_ms = best_t;
   return SN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sn_tune_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, int key_bytes,
+                     sn_stream_t stream, sn_tuning* out, float* best_ms) {
+  return tune(keys, vals, offsets, nseg, key_bytes, stream, out, best_ms, sn::SegMode::kNetworkWarpRss);
+}
+
+int sn_tune_rss_segments(void* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, int key_bytes,
+                         sn_stream_t stream, sn_tuning* out, float* best_ms) {
+  return tune(keys, vals, offsets, nseg, key_bytes, stream, out, best_ms, sn::SegMode::kRssOnly);
 }
 
 int sn_tuning_save(const char* path) {

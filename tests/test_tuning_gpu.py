@@ -94,6 +94,18 @@ def test_autotuner_installs_its_choice_and_sorts(tmp_path, restore_defaults):
     assert sn.sn_tuning_get(8, True) == params
 
 
+def test_rss_autotuner_times_the_rss_call(restore_defaults):
+    # the RSS-mode search leaves a batch sorted by rss_sort_segments, with
+    # every segment over 16 items through Register Sample Sort
+    k, _, off = wl.segment_batch(1 << 16, "uniform", "zipf", np.uint32, False, seed=81, lo=17, hi=256)
+    ek = oracle.sort_segments(k, None, off)[0]
+    dk, d_off = to_dev(k), to_dev(off)
+    params, ms = sn.sn_tune_segments(dk, None, d_off, rss_only=True)
+    assert ms > 0 and params["tile_mode"] == 0
+    assert sn.sn_tuning_get(4, False) == params
+    assert np.array_equal(to_host(dk, np.uint32), ek)
+
+
 @pytest.mark.parametrize("dtype,with_vals", [(np.uint64, True), (np.uint32, False), (np.uint32, True), (np.uint64, False)])
 @pytest.mark.parametrize("lengths,lo,hi", [("geometric", 1, 256), ("uniform", 0, 40)])
 def test_synchronous_tile_mode_many_tiles(dtype, with_vals, lengths, lo, hi, restore_defaults):
