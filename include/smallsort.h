@@ -176,7 +176,7 @@ int sn_sort_segments_u64_noalloc(uint64_t *keys, uint32_t *vals, const uint32_t 
  * results.
  */
 typedef struct {
-    int tile_units;        /* segments + items per tile of the network kernel: 512..8192 (default 4096) */
+    int tile_units;        /* segments + items per tile of the network kernel: 512..16384 (default 4096) */
     unsigned net_classes;  /* padded network sizes for 2..16-item segments: bit 0 = 2, bit 1 = 4,
                               bit 2 = 8, bit 3 = 12 channels; 16 channels always.  Bit 4: segments
                               of 33..64 items take a 64-channel warp network instead of Register

@@ -36,7 +36,7 @@ cudaError_t launch_fixed_f64(double* keys, int n, uint64_t count, int family, cu
 enum class SegMode : int { kNetworkWarpRss = 0, kRssOnly = 1 };
 
 struct SegTuning {
-  int tile_units = 4096;       // segments + elements per tile (512..8192)
+  int tile_units = 4096;       // segments + elements per tile (512..16384)
   uint32_t net_classes = 0x1F;  // bits 0..3: padded classes 2, 4, 8, 12 channels (16 always);
                                 // bit 4: 64-channel warp network for 33..64 items
   int rss_two_min = 160;       // RSS segments longer than this take a 64-item sample, else 32 (16..256)

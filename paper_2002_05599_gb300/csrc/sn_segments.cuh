@@ -1592,14 +1592,14 @@ __global__ void __launch_bounds__(kRssThreads, rss_min_blocks<K, kVals>())
 // ------------------------------------------------------------ host side ----
 
 constexpr int kCacheDevices = 64;
-constexpr int kCacheTileSizes = 7;  // tile_units 512, 1024, 2048, 3072, 4096, 6144, 8192; others are not cached
+constexpr int kCacheTileSizes = 9;  // tile_units 512, 1024, 2048, 3072, 4096, 6144, 8192, 12288, 16384; others are not cached
 
 // Cache entry of a launch shape for device d, tile size E and staging depth
 // (null: do not cache).
 inline std::atomic<int>* cache_slot(std::atomic<int>* cache, const DeviceInfo& d, uint32_t E, int stages) {
   int t = 0;
   if (E) {
-    static const uint32_t kSizes[kCacheTileSizes] = {512, 1024, 2048, 3072, 4096, 6144, 8192};
+    static const uint32_t kSizes[kCacheTileSizes] = {512, 1024, 2048, 3072, 4096, 6144, 8192, 12288, 16384};
     t = -1;
     for (int q = 0; q < kCacheTileSizes; ++q)
       if (kSizes[q] == E) t = q;
@@ -1618,7 +1618,7 @@ constexpr size_t kTileSmemLimit = 232448 - 4096;
 // kernel (mode 1).
 template <class K, bool kVals>
 bool tile_fits(int E, int stages, int mode) {
-  if (E < 512 || E > 8192 || stages < 2 || stages > kMaxStages) return false;
+  if (E < 512 || E > 16384 || stages < 2 || stages > kMaxStages) return false;
   const uint32_t e = static_cast<uint32_t>(E);
   const size_t bytes = mode == 1 ? TileLayout<K, kVals>(e).total(stages) : RingLayout<K, kVals>(e).total(stages);
   // work items of one tile: a network item holds 32 segments of >= 3 units

@@ -29,7 +29,7 @@ bool g_touched[kDevs][2][2];
 }  // namespace
 
 bool tuning_valid(const SegTuning& t) {
-  return t.tile_units >= 512 && t.tile_units <= 8192 && t.net_classes <= 0x1Fu && t.rss_two_min >= 16 &&
+  return t.tile_units >= 512 && t.tile_units <= 16384 && t.net_classes <= 0x1Fu && t.rss_two_min >= 16 &&
          t.rss_two_min <= SN_MAX_SEGMENT && t.tile_stages >= 2 && t.tile_stages <= 4 && t.tile_mode >= 0 &&
          t.tile_mode <= 1;
 }
@@ -196,7 +196,7 @@ int tune(void* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, int
   // which shares the parameter set; it stays available through sn_tuning_set.
   best.tile_mode = 0;
   float best_t = time_of(best);
-  static const int kTiles[] = {512, 1024, 2048, 3072, 4096, 6144, 8192};
+  static const int kTiles[] = {512, 1024, 2048, 3072, 4096, 6144, 8192, 12288, 16384};
   static const int kStagesC[] = {2, 3, 4};
   static const int kTwo[] = {32, 64, 96, 128, 160, 192, 224, 256};
   for (int pass = 0; pass < 2 && !failed; ++pass) {

@@ -122,7 +122,7 @@ def test_tuning_argument_errors_and_file_format(lib, tmp_path):
     t = SnTuning(2048, 0xF, 160, 2, 0)
     assert L.sn_tuning_set(2, 0, ctypes.byref(t)) == -1            # key_bytes
     assert L.sn_tuning_get(4, 0, None) == -1
-    for bad in (SnTuning(256, 0xF, 160, 2, 0), SnTuning(16384, 0xF, 160, 2, 0), SnTuning(2048, 0x20, 160, 2, 0),
+    for bad in (SnTuning(256, 0xF, 160, 2, 0), SnTuning(32768, 0xF, 160, 2, 0), SnTuning(2048, 0x20, 160, 2, 0),
                 SnTuning(2048, 0xF, 8, 2, 0), SnTuning(2048, 0xF, 300, 2, 0), SnTuning(2048, 0xF, 160, 1, 0),
                 SnTuning(2048, 0xF, 160, 5, 0), SnTuning(2048, 0xF, 160, 2, 2),
                 SnTuning(8192, 0xF, 160, 4, 0), SnTuning(8192, 0xF, 160, 2, 1)):  # last two: staging too large

@@ -52,6 +52,8 @@ def test_tile_size_limit_by_shared_memory(restore_defaults):
     # ring kernel (packed stages): a stage takes max(6, key + payload bytes) per
     # unit of tile_units + 256, and a block at most 223 KB
     assert sn.sn_tuning_set(4, False, tile_units=8192, tile_stages=4) == sn.SN_OK   # 6 B per unit
+    assert sn.sn_tuning_set(4, False, tile_units=16384, tile_stages=2) == sn.SN_OK
+    assert sn.sn_tuning_set(4, False, tile_units=16384, tile_stages=3) == sn.SN_EINVAL
     for kb, v in ((4, True), (8, False)):                                           # 8 B per unit
         assert sn.sn_tuning_set(kb, v, tile_units=8192, tile_stages=3) == sn.SN_OK
         assert sn.sn_tuning_set(kb, v, tile_units=8192, tile_stages=4) == sn.SN_EINVAL
@@ -65,10 +67,12 @@ def test_tile_size_limit_by_shared_memory(restore_defaults):
     # the largest shapes sort correctly
     k, _, off = wl.segment_batch(50_000, "geometric", "uniform", np.uint32, False, seed=79, p=0.15, cap=256)
     dk = to_dev(k)
-    sn.check(sn.sn_tuning_set(4, False, tile_units=8192, tile_stages=4), "set")
-    sn.check(sn.sn_sort_segments(dk, None, to_dev(off)), "sort")
-    assert sn.sn_check() == sn.SN_OK
-    assert np.array_equal(to_host(dk, np.uint32), oracle.sort_segments(k, None, off)[0])
+    for units, stages in ((8192, 4), (16384, 2)):
+        dk = to_dev(k)
+        sn.check(sn.sn_tuning_set(4, False, tile_units=units, tile_stages=stages), "set")
+        sn.check(sn.sn_sort_segments(dk, None, to_dev(off)), "sort")
+        assert sn.sn_check() == sn.SN_OK
+        assert np.array_equal(to_host(dk, np.uint32), oracle.sort_segments(k, None, off)[0]), units
     k, v, off = wl.segment_batch(60_000, "geometric", "fewdistinct", np.uint64, True, seed=80, p=0.15, cap=256)
     ek, ev = oracle.sort_segments(k, v, off)
     for units, stages in ((8192, 2), (6144, 2), (4096, 4), (3072, 3)):
