@@ -115,6 +115,35 @@ def test_server_argument_errors(lib):
         assert create(ctypes.byref(ServerConfig(1 << 20, 4, 4, 0, 0, 0)), ctypes.byref(h)) in (-4, -6)
 
 
+def test_tile_shape_limits(lib):
+    # Shared-memory and task-ring limits of the tile shapes, checked before any
+    # device is touched (a shape that passes gets past SN_EINVAL; on a machine
+    # without a GPU the call then fails on the device instead).  Ring kernel:
+    # a packed stage takes max(6, key + payload bytes) per unit of
+    # tile_units + 256 bytes; synchronous kernel: fixed regions.
+    import paper_2002_05599_gb300 as sn
+    from paper_2002_05599_gb300._binding import SnTuning
+    L = sn._binding._tune_lib()
+
+    def fits(kb, vals, units, stages, mode=0):
+        return L.sn_tuning_set(kb, vals, ctypes.byref(SnTuning(units, 0x1F, 160, stages, mode))) != -1
+
+    assert fits(4, 0, 16384, 2) and not fits(4, 0, 16384, 3)    # 6 B per unit
+    assert fits(4, 0, 8192, 4)
+    for kb, v in ((4, 1), (8, 0)):                               # 8 B per unit
+        assert fits(kb, v, 8192, 3) and not fits(kb, v, 8192, 4)
+        assert not fits(kb, v, 16384, 2)
+    assert fits(8, 1, 8192, 2) and not fits(8, 1, 8192, 3)      # 12 B per unit
+    assert fits(8, 1, 6144, 2) and fits(8, 1, 4096, 4)
+    assert fits(4, 0, 8192, 2, 1)                                # synchronous kernel
+    for kb, v in ((4, 1), (8, 0), (8, 1)):
+        assert not fits(kb, v, 8192, 2, 1) and fits(kb, v, 4096, 2, 1)
+    assert not fits(4, 0, 32768, 2) and not fits(4, 0, 256, 2)
+    for kb in (4, 8):  # on a GPU machine the shapes above were installed: back to the defaults
+        for v in (False, True):
+            sn.sn_tuning_set(kb, v)
+
+
 def test_tuning_argument_errors_and_file_format(lib, tmp_path):
     import paper_2002_05599_gb300 as sn
     from paper_2002_05599_gb300._binding import SnTuning
