@@ -106,8 +106,8 @@ int sn_sort_segments_f64(double *keys, uint32_t *vals, const uint32_t *offsets, 
                          sn_stream_t stream);
 
 /*
- * CSR segments (spec batching layer; the paper's Sec. 5 suggests
- * bucketing base cases by size and solving batches of equal size).
+ * CSR segments (the batching layer: the paper's Sec. 5 suggests bucketing
+ * base cases by size and solving batches of equal size).
  *
  * offsets: nseg+1 u32 entries; segment i is keys[offsets[i] .. offsets[i+1]).
  *          Must be non-decreasing with every length <= 256.  A violation is
