@@ -159,6 +159,8 @@ def test_tuning_argument_errors_and_file_format(lib, tmp_path):
     L.sn_tune_segments.argtypes = L.sn_tune_segments.argtypes
     assert L.sn_tune_segments(None, None, None, 5, 4, None, None, None) == -1
     assert L.sn_tune_segments(0x1000, None, 0x2000, 5, 3, None, None, None) == -1
+    assert L.sn_tune_rss_segments(None, None, None, 5, 4, None, None, None) == -1
+    assert L.sn_tune_rss_segments(0x1000, None, 0x2000, 5, 3, None, None, None) == -1
     assert sn.sn_tuning_save(os.path.join(tmp_path, "no", "such", "dir.txt")) == -1
     bad_file = os.path.join(tmp_path, "bad.txt")
     with open(bad_file, "w") as f:
