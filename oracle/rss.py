@@ -69,20 +69,6 @@ def classify_definition(e, splitters: list) -> int:
     raise AssertionError("splitters not sorted")
 
 
-def classify_algorithm1(e, s0, s1, s2) -> int:
-    """Algorithm 1 (three splitters): compare with the root splitter1, copy the
-    left subtree (splitter0) and overwrite it with the right one (splitter2)
-    when the element is larger, then append the second comparison's bit."""
-    cmp_result = 1 if s1 < e else 0
-    splitterx = s0
-    if cmp_result:
-        splitterx = s2
-    index = cmp_result
-    cmp_result = 1 if splitterx < e else 0
-    index = (index << 1) + cmp_result
-    return index
-
-
 def rss_sort(items: list, k: int = 4, a: int = 3, base: int = 16, base_sort=sorted) -> list:
     """Sort distinct, comparable items by Register Sample Sort with k buckets."""
     n = len(items)

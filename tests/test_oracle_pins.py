@@ -109,10 +109,30 @@ def test_perm_product_definition_and_invariants():
     assert oracle.perm_check_z(c) == oracle.PERM_Z + 1
 
 
-def test_is_sorted_segments():
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_is_sorted_segments(dtype):
+    # Sec. 4.1's sorted check, per segment: a descent across a segment
+    # boundary or inside an empty segment's neighbourhood is allowed, equal
+    # neighbours are sorted, any descent inside a segment is not
     off = np.array([0, 3, 3, 5], dtype=np.uint32)
-    assert oracle.is_sorted_segments(np.array([1, 2, 2, 0, 9], dtype=np.uint64), off)
-    assert not oracle.is_sorted_segments(np.array([1, 2, 2, 9, 8], dtype=np.uint64), off)
+    assert oracle.is_sorted_segments(np.array([1, 2, 2, 0, 9], dtype=dtype), off)
+    assert not oracle.is_sorted_segments(np.array([1, 2, 2, 9, 8], dtype=dtype), off)
+    assert not oracle.is_sorted_segments(np.array([2, 1, 2, 0, 9], dtype=dtype), off)  # first pair
+    top = np.iinfo(dtype).max
+    assert oracle.is_sorted_segments(np.array([top, top, top], dtype=dtype), np.array([0, 3], np.uint32))
+    assert not oracle.is_sorted_segments(np.array([top, 0], dtype=dtype), np.array([0, 2], np.uint32))
+    # against a direct Python check on random batches with a few planted descents
+    rng = np.random.default_rng(17)
+    k, _, off = wl.segment_batch(300, "geometric", "fewdistinct", dtype, False, seed=18)
+    srt, _ = oracle.sort_segments(k, None, off)
+    assert oracle.is_sorted_segments(srt, off)
+    for _ in range(30):
+        bad = srt.copy()
+        i = int(rng.integers(1, bad.size))
+        bad[i - 1], bad[i] = bad[i], bad[i - 1]
+        expect = all(bad[e - 1] <= bad[e] for s in range(off.size - 1)
+                     for e in range(int(off[s]) + 1, int(off[s + 1])))
+        assert oracle.is_sorted_segments(bad, off) == expect
 
 
 # --------------------------------------------------------------- networks ----
@@ -166,6 +186,25 @@ def test_perm_and_01_checkers_agree(golden_networks):
                (oracle.network_failures_01(n6, broken) > 0)
 
 
+def _perm_failures_python(n, pairs):
+    fails = 0
+    for p in itertools.permutations(range(n)):
+        x = list(p)
+        for i, j in pairs:
+            if x[i] > x[j]:
+                x[i], x[j] = x[j], x[i]
+        fails += x != sorted(x)
+    return fails
+
+
+def test_perm_checker_counts_like_brute_force(golden_networks):
+    n6, _, lv6 = golden_networks["bn6"]
+    p6 = [p for lv in lv6 for p in lv]
+    for c in (0, 5, len(p6) - 1):
+        broken = p6[:c] + p6[c + 1:]
+        assert oracle.network_failures_perm(n6, broken) == _perm_failures_python(n6, broken)
+
+
 def test_wide_01_checker_matches_plain(golden_networks):
     rng = np.random.default_rng(11)
     for name in ["best16", "opt10", "bnl16"]:
@@ -205,15 +244,6 @@ def test_rss_tree_classification_matches_definition():
         assert tree[1] == spl[k // 2 - 1]  # root is s_(k/2)
         for e in range(-2, 1003):
             assert rss.classify_tree(e, tree) == rss.classify_definition(e, spl)
-
-
-def test_rss_algorithm1_matches_tree():
-    rng = np.random.default_rng(4)
-    for _ in range(200):
-        s = sorted(rng.choice(100, size=3, replace=False).tolist())
-        tree = rss.heap_tree(s)
-        for e in range(-1, 102):
-            assert rss.classify_algorithm1(e, *s) == rss.classify_tree(e, tree)
 
 
 @pytest.mark.parametrize("k,a", [(4, 3), (4, 1), (8, 2), (16, 2), (32, 3)])
@@ -328,6 +358,80 @@ def test_float_keys_on_random_bit_patterns_against_python():
         assert np.array_equal(gk[lo:hi], kf[order]) and np.array_equal(gv[lo:hi], v[order])
 
 
+
+def _total_order_key64(bits):
+    """IEEE 754 totalOrder of a binary64 bit pattern as a Python sort key, from
+    the standard's cases: NaNs (exponent all ones, fraction non-zero) with the
+    sign bit set come before everything and order by decreasing payload, those
+    without it after everything by increasing payload; other values order by
+    numeric value, with -0 before +0."""
+    import math
+    bits = int(bits)
+    if (bits >> 52) & 0x7FF == 0x7FF and bits & ((1 << 52) - 1):
+        payload = bits & ((1 << 63) - 1)
+        return (0, -payload) if bits >> 63 else (2, payload)
+    x = float(np.array([bits], np.uint64).view(np.float64)[0])  # exact for non-NaN
+    return (1, x, 0 if math.copysign(1.0, x) < 0 else 1)
+
+
+# binary64 bit patterns in totalOrder, written out from the standard's cases:
+# negative NaNs (largest payload first; quiet and signalling), -inf, negative
+# normal and subnormal numbers, -0, +0, positive numbers, +inf, positive NaNs.
+_F64_ORDERED = [
+    0xFFFFFFFFFFFFFFFF, 0xFFF8000000000001, 0xFFF8000000000000, 0xFFF4000000000000, 0xFFF0000000000001,
+    0xFFF0000000000000, 0xFFEFFFFFFFFFFFFF, 0xBFF0000000000000, 0x800FFFFFFFFFFFFF, 0x8000000000000001,
+    0x8000000000000000, 0x0000000000000000, 0x0000000000000001, 0x000FFFFFFFFFFFFF, 0x3FF0000000000000,
+    0x7FEFFFFFFFFFFFFF, 0x7FF0000000000000, 0x7FF0000000000001, 0x7FF4000000000000, 0x7FF8000000000000,
+    0x7FF8000000000001, 0x7FFFFFFFFFFFFFFF,
+]
+
+
+def test_f64_keys_follow_total_order_on_special_values():
+    expect = np.array(_F64_ORDERED, np.uint64)
+    # the written-out order agrees with the case-by-case key (two independent statements)
+    assert sorted(_F64_ORDERED, key=_total_order_key64) == _F64_ORDERED
+    rng = np.random.default_rng(13)
+    for _ in range(20):
+        shuffled = rng.permutation(expect).view(np.float64)
+        got = oracle.sort_fixed(shuffled, expect.size)
+        assert np.array_equal(got.view(np.uint64), expect)
+
+
+def _f64_mix(rng, size):
+    """binary64 bit patterns from a small pool of special values (both NaN
+    signs with several payloads, signed zeros, infinities) and random bits."""
+    pool = np.array(_F64_ORDERED, np.uint64)
+    bits = rng.integers(0, 2**63, size, dtype=np.uint64) | (rng.integers(0, 2, size, dtype=np.uint64) << np.uint64(63))
+    pick = rng.random(size) < 0.6
+    bits[pick] = rng.choice(pool, int(pick.sum()))
+    return bits
+
+
+def test_f64_keys_on_random_bit_patterns_against_python():
+    rng = np.random.default_rng(14)
+    bits = _f64_mix(rng, 8 * 1500)
+    got = oracle.sort_fixed(bits.view(np.float64), 8).view(np.uint64).reshape(-1, 8)
+    for a, row in enumerate(bits.reshape(-1, 8)):
+        order = sorted(range(8), key=lambda i: (_total_order_key64(row[i]), i))
+        assert np.array_equal(got[a], row[order])
+
+
+def test_f64_segments_stable_against_python():
+    # oracle_sort_segments_f64: equal bit patterns (many, from the small pool)
+    # keep their input order and the payload moves with its key
+    rng = np.random.default_rng(15)
+    _, v, off = wl.segment_batch(400, "geometric", "uniform", np.uint64, True, seed=16)
+    bits = _f64_mix(rng, int(off[-1]))
+    gk, gv = oracle.sort_segments(bits.view(np.float64), v, off)
+    gk = gk.view(np.uint64)
+    for sgm in range(off.size - 1):
+        lo, hi = int(off[sgm]), int(off[sgm + 1])
+        order = sorted(range(lo, hi), key=lambda i: (_total_order_key64(bits[i]), i))
+        assert np.array_equal(gk[lo:hi], bits[order]) and np.array_equal(gv[lo:hi], v[order])
+    # keys only (no payload) gives the same keys
+    gk2, gv2 = oracle.sort_segments(bits.view(np.float64), None, off)
+    assert gv2 is None and np.array_equal(gk2.view(np.uint64), gk)
+
 _MUTATIONS = {
     # a wrong comparison sign in the fixed-size insertion sort
     "fixed_sign": ("while (j >= 0 && A[j] > x) {\n                A[j + 1] = A[j];\n                --j;\n            }\n            A[j + 1] = x;\n        }\n    }\n}\n\nvoid oracle_sort_fixed_u64",
@@ -360,6 +464,37 @@ _MUTATIONS = {
     # the permutation product drops a term
     "perm": ("    for (uint64_t i = 0; i < len; ++i) {\n        uint64_t ar = a[i] % p;",
              "    for (uint64_t i = 1; i < len; ++i) {\n        uint64_t ar = a[i] % p;"),
+    # the u32 permutation product drops its last term
+    "perm_u32": ("    for (uint64_t i = 0; i < len; ++i) {\n        uint64_t ar = (uint64_t)a[i] % p;",
+                 "    for (uint64_t i = 0; i + 1 < len; ++i) {\n        uint64_t ar = (uint64_t)a[i] % p;"),
+    # a wrong comparison sign in the u64 fixed-size sort
+    "fixed_u64_sign": ("while (j >= 0 && A[j] > x) {\n                A[j + 1] = A[j];\n                --j;\n            }\n            A[j + 1] = x;\n        }\n    }\n}\n\n/*\n * The 16-byte items",
+                       "while (j >= 0 && A[j] < x) {\n                A[j + 1] = A[j];\n                --j;\n            }\n            A[j + 1] = x;\n        }\n    }\n}\n\n/*\n * The 16-byte items"),
+    # an unstable u64 segment sort
+    "seg_u64_unstable": ("while (j >= 0 && A[j] > x) {\n                A[j + 1] = A[j];\n                if (V) V[j + 1] = V[j];\n                --j;\n            }\n            A[j + 1] = x;\n            if (V) V[j + 1] = v;\n        }\n    }\n}\n\n/*\n * One array",
+                         "while (j >= 0 && A[j] >= x) {\n                A[j + 1] = A[j];\n                if (V) V[j + 1] = V[j];\n                --j;\n            }\n            A[j + 1] = x;\n            if (V) V[j + 1] = v;\n        }\n    }\n}\n\n/*\n * One array"),
+    # f32: -0 and +0 in the wrong order
+    "f32_zero": ("        return (signbit(a) == 0) && (signbit(b) != 0);\n    }\n    uint32_t pa, pb;",
+                 "        return (signbit(a) != 0) && (signbit(b) == 0);\n    }\n    uint32_t pa, pb;"),
+    # f64: negative NaNs ordered by payload the wrong way (as if positive)
+    "f64_nan_payload": ("    pa &= 0x7FFFFFFFFFFFFFFFull;\n    pb &= 0x7FFFFFFFFFFFFFFFull;\n    return ca > 0 ? pa > pb : pa < pb;",
+                        "    pa &= 0x7FFFFFFFFFFFFFFFull;\n    pb &= 0x7FFFFFFFFFFFFFFFull;\n    return pa > pb;"),
+    # f64: the NaN classes in the wrong order (negative NaNs last)
+    "f64_nan_class": ("    if (ca != cb) return ca > cb;\n    if (ca == 0) {\n        if (a != b) return a > b;\n        return (signbit(a) == 0) && (signbit(b) != 0); /* +0 after -0 */",
+                      "    if (ca != cb) return ca < cb;\n    if (ca == 0) {\n        if (a != b) return a > b;\n        return (signbit(a) == 0) && (signbit(b) != 0); /* +0 after -0 */"),
+    # f64 segments: the payload is not moved with its key
+    "seg_f64_payload": ("            while (j >= 0 && greater_f64(A[j], x)) {\n                A[j + 1] = A[j];\n                if (V) V[j + 1] = V[j];",
+                        "            while (j >= 0 && greater_f64(A[j], x)) {\n                A[j + 1] = A[j];"),
+    # the u32 sorted check skips the first pair of every segment
+    "sorted_u32": ("int oracle_is_sorted_segments_u32(const uint32_t *keys, const uint32_t *offsets, uint64_t nseg)\n{\n    for (uint64_t s = 0; s < nseg; ++s)\n        for (uint64_t i = (uint64_t)offsets[s] + 1;",
+                   "int oracle_is_sorted_segments_u32(const uint32_t *keys, const uint32_t *offsets, uint64_t nseg)\n{\n    for (uint64_t s = 0; s < nseg; ++s)\n        for (uint64_t i = (uint64_t)offsets[s] + 2;"),
+    # the u64 sorted check rejects equal neighbours
+    "sorted_u64": ("            if (keys[i - 1] > keys[i]) return 0;\n    return 1;\n}\n\nint oracle_is_sorted_segments_u32",
+                   "            if (keys[i - 1] >= keys[i]) return 0;\n    return 1;\n}\n\nint oracle_is_sorted_segments_u32"),
+    # the permutation checker feeds values with pairs made equal
+    "perm_values": ("        for (int i = 0; i < n; ++i) x[i] = p[i];\n", "        for (int i = 0; i < n; ++i) x[i] = p[i] / 2;\n"),
+    # the wide 0-1 checker gives channels 0 and 1 the same input bits
+    "wide_pattern": ("0xAAAAAAAAAAAAAAAAull, 0xCCCCCCCCCCCCCCCCull,", "0xAAAAAAAAAAAAAAAAull, 0xAAAAAAAAAAAAAAAAull,"),
 }
 
 
@@ -393,6 +528,31 @@ def _pins_pass(lib_path, golden):
         special64 = np.array([0x8000000000000000, 0, 0xBFF0000000000000, 0x7FF8000000000000], np.uint64)
         ok &= np.array_equal(oracle.sort_fixed(special64[[1, 3, 0, 2]].view(np.float64), 4).view(np.uint64),
                              special64[[2, 0, 1, 3]])
+        keys64 = wl.fixed_arrays(8, 64, "uniform", np.uint64, seed=9)
+        ok &= np.array_equal(oracle.sort_fixed(keys64, 8), np.sort(keys64.reshape(-1, 8), 1).reshape(-1))
+        f64 = np.array(_F64_ORDERED, np.uint64)
+        got = oracle.sort_fixed(np.random.default_rng(9).permutation(f64).view(np.float64), f64.size)
+        ok &= np.array_equal(got.view(np.uint64), f64)
+        rng = np.random.default_rng(10)
+        _, v, off = wl.segment_batch(60, "geometric", "uniform", np.uint64, True, seed=10)
+        bits = _f64_mix(rng, int(off[-1]))
+        gk, gv = oracle.sort_segments(bits.view(np.float64), v, off)
+        for sgm in range(off.size - 1):
+            lo, hi = int(off[sgm]), int(off[sgm + 1])
+            order = sorted(range(lo, hi), key=lambda i: (_total_order_key64(bits[i]), i))
+            ok &= np.array_equal(gk.view(np.uint64)[lo:hi], bits[order]) and np.array_equal(gv[lo:hi], v[order])
+        for dt in (np.uint32, np.uint64):
+            soff = np.array([0, 3, 3, 5], dtype=np.uint32)
+            ok &= oracle.is_sorted_segments(np.array([1, 2, 2, 0, 9], dtype=dt), soff)
+            ok &= not oracle.is_sorted_segments(np.array([2, 1, 2, 0, 9], dtype=dt), soff)
+        a32 = np.arange(1, 40, dtype=np.uint32)
+        expect32 = 1
+        for x in a32.tolist():
+            expect32 = expect32 * ((oracle.PERM_Z - x) % oracle.PERM_P) % oracle.PERM_P
+        ok &= oracle.perm_product(a32) == expect32
+        n6, _, lv6 = golden["bn6"]
+        p6 = [p for lv in lv6 for p in lv]
+        ok &= oracle.network_failures_perm(n6, p6[:-1]) == _perm_failures_python(n6, p6[:-1])
         items = _random_items(40, 7, seed=9)
         ok &= np.array_equal(oracle.sort_fixed_items(items, 7), _items_reference(items, 7))
         arr = wl.uniform_keys(3001, np.uint32, 9) % np.uint32(500)
