@@ -227,6 +227,19 @@ int sn_tuning_save(const char *path);
 int sn_tuning_load(const char *path);
 
 /*
+ * Tuning in one call.  If `path` names a readable file written by
+ * sn_tuning_save, loads it (sn_tuning_load's result).  Otherwise runs
+ * sn_tune_segments for u32 and u64 keys, each with and without payload, on a
+ * built-in synthetic batch (2^20 segments, lengths geometric(0.15) capped at
+ * 256, uniform keys; about 60 MB of device memory allocated and freed with
+ * cudaMalloc / cudaFree, so the call synchronises the device), installs the
+ * four sets on the current device and, if `path` is not NULL, writes them to
+ * it with sn_tuning_save.  The file format is sn_tuning_save's text format.
+ * Returns SN_OK or the first failing step's status.
+ */
+int sn_tune(const char *path);
+
+/*
  * Segments longer than 256 items (library addition; the paper names merging
  * networks as the way beyond its 256-item range, Sec. 5).  Same contract as
  * sn_sort_segments / _u64, for lengths 0..SN_MAX_SEGMENT_LARGE: one thread
@@ -266,6 +279,28 @@ int sn_sort_large(uint32_t *keys, uint64_t n, sn_stream_t stream);
  * of concurrent calls on other streams are reported together.
  */
 int sn_check(sn_stream_t stream);
+
+/*
+ * The device-wide form of sn_check: synchronises the current device (every
+ * stream), then returns and clears its status word with the same mapping as
+ * sn_check; SN_ECUDA if the device or an earlier asynchronous launch reported
+ * a CUDA error.  For callers that do not track which stream a failed call
+ * used.
+ */
+int sn_get_last_cuda_error(void);
+
+/*
+ * Limit of the bounded device waits (a library safeguard; the paper's CPU
+ * code has no device waits).  Every wait inside this library's kernels -- for
+ * a staged copy, a work item, a free staging buffer -- gives up after `ns`
+ * nanoseconds of GPU time (2 s by default), records SN_ETIMEOUT in the status
+ * word and lets its kernel return, so no library kernel can spin forever.
+ * Applies to the current device; `ns` in [1000, 6e10], else SN_EINVAL.
+ * Synchronous (a 16-byte copy to the device); call it while no library work
+ * runs on the device.  A limit shorter than a kernel's normal waits makes
+ * calls fail with SN_ETIMEOUT and leaves their data partly sorted.
+ */
+int sn_set_wait_limit(uint64_t ns);
 
 /* Short English description of a status code (static storage). */
 const char *sn_status_string(int status);

@@ -88,9 +88,14 @@ int sn_server_submit(sn_server *srv, const void *keys_in, const uint32_t *vals_i
 
 /*
  * Waits up to timeout_ns (0 = poll, negative = forever) for request `ticket`.
- * Returns its status (SN_OK, or SN_ECUDA if its batch failed) once it has
- * completed, and forgets the ticket; SN_ETIMEOUT if it is still running;
- * SN_EINVAL for an unknown or already collected ticket.
+ * Returns its status once it has completed, and forgets the ticket: SN_OK;
+ * SN_ERANGE if the device found its batch's offsets invalid; SN_ECUDA if its
+ * batch failed (a CUDA error, a bounded device wait that ran out, an internal
+ * check) -- every request of a batch gets the batch's status, which comes from
+ * a status word of the batch's own, so failures of other batches or calls do
+ * not leak into it.  SN_ETIMEOUT if it is still running; SN_EINVAL for an
+ * unknown or already collected ticket (also when another thread waiting on the
+ * same ticket collected it first).
  */
 int sn_server_wait(sn_server *srv, uint64_t ticket, int64_t timeout_ns);
 

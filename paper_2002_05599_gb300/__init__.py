@@ -29,6 +29,7 @@ from ._binding import (  # noqa: F401
     rss_sort_segments,
     rss_sort_segments_u64,
     sn_check,
+    sn_get_last_cuda_error,
     sn_sort_fixed,
     sn_sort_fixed_f32,
     sn_sort_fixed_f64,
@@ -43,6 +44,7 @@ from ._binding import (  # noqa: F401
     sn_sort_segments_large_u64,
     sn_sort_segments_u64,
     sn_status_string,
+    sn_tune,
     sn_tune_segments,
     sn_tuning_get,
     sn_tuning_load,

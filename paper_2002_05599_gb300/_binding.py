@@ -262,9 +262,26 @@ def sn_tuning_load(path: str) -> int:
     return _tune_lib().sn_tuning_load(os.fsencode(path))
 
 
+def sn_tune(path: str | None = None) -> int:
+    """Load a saved parameter table from ``path``, or tune every key type and
+    payload kind on the library's synthetic batch (and save to ``path``)."""
+    lib = _tune_lib()
+    lib.sn_tune.argtypes = [ctypes.c_char_p]
+    lib.sn_tune.restype = ctypes.c_int
+    return lib.sn_tune(None if path is None else os.fsencode(path))
+
+
 def sn_check(stream=None) -> int:
     """Synchronise the stream; return and clear the device status word."""
     return library().sn_check(_stream(stream))
+
+
+def sn_get_last_cuda_error() -> int:
+    """Synchronise the device; return and clear the device status word."""
+    lib = library()
+    lib.sn_get_last_cuda_error.argtypes = []
+    lib.sn_get_last_cuda_error.restype = ctypes.c_int
+    return lib.sn_get_last_cuda_error()
 
 
 def sn_status_string(status: int) -> str:

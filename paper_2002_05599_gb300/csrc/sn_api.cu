@@ -5,14 +5,16 @@
 #include <mutex>
 
 #include "smallsort.h"
+#include "smallsort_testing.h"
 #include "sn_common.cuh"
 #include "sn_internal.h"
 #include "sn_seg_scratch.h"
 
 namespace sn {
 
-// Per-device status word, OR-ed by kernels (kStatusRange, kStatusTimeout).
-__device__ unsigned g_status;
+// Per-device control block: the status word OR-ed by kernels (kStatusRange,
+// kStatusTimeout, ...), the test flags and the limit of every bounded wait.
+__device__ DevCtl g_ctl = {0u, 0u, kDefaultWaitLimitNs};
 
 namespace {
 
@@ -29,8 +31,8 @@ int init_device(int dev, DeviceInfo* out) {
   if (cudaDeviceGetAttribute(&d.cc_minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return SN_ECUDA;
   if (d.cc_major != 10 || d.cc_minor != 3) return SN_EUNSUPPORTED;  // built for sm_103a only
   void* p = nullptr;
-  if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return SN_EUNSUPPORTED;
-  d.status = static_cast<unsigned*>(p);
+  if (cudaGetSymbolAddress(&p, g_ctl) != cudaSuccess) return SN_EUNSUPPORTED;
+  d.status = &static_cast<DevCtl*>(p)->status;
   cudaMemPoolProps props = {};
   props.allocType = cudaMemAllocationTypePinned;
   props.location.type = cudaMemLocationTypeDevice;
@@ -71,6 +73,13 @@ const DeviceInfo* device_info(int* err) {
   }
   *err = SN_OK;
   return &g_info[dev];
+}
+
+int status_from_word(unsigned word) {
+  if (word & kStatusRange) return SN_ERANGE;
+  if (word & kStatusTimeout) return SN_ETIMEOUT;
+  if (word & (kStatusInternal | kCheckStageMoved | kCheckCopyArgs | kCheckSegment)) return SN_ECUDA;
+  return SN_OK;
 }
 
 }  // namespace sn
@@ -260,6 +269,10 @@ std::atomic<unsigned> g_last_word{0};
 // of the public interface).
 unsigned sn_debug_status_word(void) { return g_last_word.load(); }
 
+namespace {
+int status_of_word(unsigned word) { return sn::status_from_word(word); }
+}  // namespace
+
 int sn_check(sn_stream_t stream) {
   int err = SN_OK;
   const sn::DeviceInfo* d = sn::device_info(&err);
@@ -271,10 +284,40 @@ int sn_check(sn_stream_t stream) {
   if (sn::clear_status(*d, s) != cudaSuccess) return SN_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return SN_ECUDA;
   g_last_word.store(word);
-  if (word & sn::kStatusRange) return SN_ERANGE;
-  if (word & sn::kStatusTimeout) return SN_ETIMEOUT;
-  if (word & (sn::kStatusInternal | sn::kCheckStageMoved | sn::kCheckCopyArgs | sn::kCheckSegment)) return SN_ECUDA;
-  return SN_OK;
+  return status_of_word(word);
+}
+
+int sn_get_last_cuda_error(void) {
+  int err = SN_OK;
+  const sn::DeviceInfo* d = sn::device_info(&err);
+  if (d == nullptr) return err;
+  // every stream of the device: errors of earlier asynchronous calls surface here
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) return SN_ECUDA;
+  unsigned word = 0;
+  if (cudaMemcpy(&word, d->status, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess) return SN_ECUDA;
+  if (cudaMemset(d->status, 0, sizeof(word)) != cudaSuccess) return SN_ECUDA;
+  g_last_word.store(word);
+  return status_of_word(word);
+}
+
+int sn_set_wait_limit(uint64_t ns) {
+  if (ns < 1000ull || ns > 60000000000ull) return SN_EINVAL;
+  int err = SN_OK;
+  const sn::DeviceInfo* d = sn::device_info(&err);
+  if (d == nullptr) return err;
+  const unsigned long long v = ns;
+  sn::DevCtl* ctl = reinterpret_cast<sn::DevCtl*>(d->status);
+  return cudaMemcpy(&ctl->wait_limit_ns, &v, sizeof(v), cudaMemcpyHostToDevice) == cudaSuccess ? SN_OK : SN_ECUDA;
+}
+
+int sn_test_set_flags(unsigned flags) {
+  if (flags & ~(sn::kTestSkipFixedCopy | sn::kTestSkipTileCopy | sn::kTestSkipRssCopy)) return SN_EINVAL;
+  int err = SN_OK;
+  const sn::DeviceInfo* d = sn::device_info(&err);
+  if (d == nullptr) return err;
+  sn::DevCtl* ctl = reinterpret_cast<sn::DevCtl*>(d->status);
+  return cudaMemcpy(&ctl->test_flags, &flags, sizeof(flags), cudaMemcpyHostToDevice) == cudaSuccess ? SN_OK
+                                                                                                   : SN_ECUDA;
 }
 
 const char* sn_status_string(int status) {
@@ -338,8 +381,8 @@ int noalloc_setup(int dev, NoAllocDevice* out) {
     return SN_ECUDA;
   if (nd.info.cc_major != 10 || nd.info.cc_minor != 3) return SN_EUNSUPPORTED;
   void* status = nullptr;
-  if (cudaGetSymbolAddress(&status, g_status) != cudaSuccess) return SN_EUNSUPPORTED;
-  nd.info.status = static_cast<unsigned*>(status);
+  if (cudaGetSymbolAddress(&status, g_ctl) != cudaSuccess) return SN_EUNSUPPORTED;
+  nd.info.status = &static_cast<DevCtl*>(status)->status;
   void* scratch = nullptr;
   if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess) return SN_EUNSUPPORTED;
   nd.scratch = scratch;

@@ -23,9 +23,35 @@ constexpr unsigned kCheckStageMoved = 8u;    // a tile's metadata changed while 
 constexpr unsigned kCheckCopyArgs = 16u;     // a bulk copy's range or alignment was invalid
 constexpr unsigned kCheckSegment = 32u;      // a segment's staged span left its buffer
 
-// Bounded mbarrier waits: a wait gives up after kWaitLimitNs of global time
-// (about two seconds) and reports failure instead of spinning forever.
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+// Per-device control block in device memory.  Kernels receive the address of
+// its first word as `unsigned* status`:
+//   status bits   OR-ed by kernels (kStatus*, kCheck*), read and cleared by
+//                 sn_check / sn_get_last_cuda_error;
+//   test flags    kTestSkip* below, zero in normal use (set only by the test
+//                 hook sn_test_set_flags);
+//   wait limit    every bounded wait gives up after this many nanoseconds of
+//                 %globaltimer, reports kStatusTimeout and lets the kernel
+//                 return (sn_set_wait_limit; two seconds by default).
+struct alignas(16) DevCtl {
+  unsigned status;
+  unsigned test_flags;
+  unsigned long long wait_limit_ns;
+};
+constexpr unsigned long long kDefaultWaitLimitNs = 2000000000ull;
+
+// Test flags: the kernel arms its copy-completion barrier but issues no copy,
+// so its own bounded wait runs out (the host-side way of exercising the
+// timeout path; nothing faults, nothing waits forever).
+constexpr unsigned kTestSkipFixedCopy = 1u;  // fixed-size kernel
+constexpr unsigned kTestSkipTileCopy = 2u;   // segmented tile kernel (producer warp)
+constexpr unsigned kTestSkipRssCopy = 4u;    // Register Sample Sort kernel
+
+__device__ __forceinline__ unsigned long long wait_limit_ns(const unsigned* status) {
+  return reinterpret_cast<const volatile DevCtl*>(status)->wait_limit_ns;
+}
+__device__ __forceinline__ unsigned test_flags(const unsigned* status) {
+  return reinterpret_cast<const volatile DevCtl*>(status)->test_flags;
+}
 
 // ------------------------------------------------------------ items -------
 
@@ -364,13 +390,15 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel_smem(uint32_t* p, uint32_t 
   return old;
 }
 
-// Wait for the phase with the given parity to complete; false once
-// kWaitLimitNs have passed without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with the given parity to complete; false once the
+// device's wait limit (read from the control block at `status`) has passed
+// without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const unsigned* status) {
   if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long limit = wait_limit_ns(status);
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit) return false;
   return true;
 }
 

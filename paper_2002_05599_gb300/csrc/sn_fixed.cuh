@@ -258,10 +258,11 @@ __global__ void __launch_bounds__(kFixedThreads)
     fence_mbar_init();
   }
   __syncthreads();
+  const bool skip_copy = tid == 0 && (test_flags(status) & kTestSkipFixedCopy);
   if (tid == 0) {
     for (uint64_t s = 0; s < kStages && s < my; ++s) {
       mbar_arrive_expect_tx(&full[s], C::kTileBytes);
-      bulk_g2s(smem + s * C::kTileBytes, tile_ptr(s), C::kTileBytes, &full[s]);
+      if (!skip_copy) bulk_g2s(smem + s * C::kTileBytes, tile_ptr(s), C::kTileBytes, &full[s]);
     }
   }
 
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kFixedThreads)
   uint64_t i = 0;
   for (; i < my; ++i) {
     const int s = static_cast<int>(i % kStages);
-    const bool ok = mbar_wait(&full[s], static_cast<uint32_t>(i / kStages) & 1u);
+    const bool ok = mbar_wait(&full[s], static_cast<uint32_t>(i / kStages) & 1u, status);
     if (ok) {
       unsigned char* buf = smem + s * C::kTileBytes;
 #pragma unroll
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(kFixedThreads)
         const int ps = static_cast<int>((i - 1) % kStages);
         bulk_wait_read<1>();  // the store of tile i-1 has read its buffer
         mbar_arrive_expect_tx(&full[ps], C::kTileBytes);
-        bulk_g2s(smem + ps * C::kTileBytes, tile_ptr(i - 1 + kStages), C::kTileBytes, &full[ps]);
+        if (!skip_copy) bulk_g2s(smem + ps * C::kTileBytes, tile_ptr(i - 1 + kStages), C::kTileBytes, &full[ps]);
       }
     }
   }
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kFixedThreads)
       // let the loads that were issued but never consumed land before exit
       const uint64_t issued_end = min(my, max(static_cast<uint64_t>(kStages), i + kStages - 1));
       for (uint64_t t = i; t < issued_end; ++t)
-        (void)mbar_wait(&full[t % kStages], static_cast<uint32_t>(t / kStages) & 1u);
+        (void)mbar_wait(&full[t % kStages], static_cast<uint32_t>(t / kStages) & 1u, status);
     }
   }
 }

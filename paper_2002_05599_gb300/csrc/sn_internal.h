@@ -20,6 +20,13 @@ struct DeviceInfo {
 // Per-device facts, initialised once per device (thread-safe).
 const DeviceInfo* device_info(int* err);
 
+// Size of the per-device control block whose first word `DeviceInfo::status`
+// points at (status word, test flags, wait limit: sn_common.cuh DevCtl).
+constexpr size_t kDevCtlBytes = 16;
+
+// The status code a device status word maps to (SN_OK if no bit is set).
+int status_from_word(unsigned word);
+
 // Fixed-size arrays (sn_fixed_*.cu; kernels in sn_fixed.cuh).  `family` is
 // SN_NETWORK_BEST or SN_NETWORK_BOSE_NELSON (u64 keys: best only).  Return a
 // cudaError_t.

@@ -1019,6 +1019,9 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
           m.key_cap = static_cast<uint32_t>(key_bytes / sizeof(K));
           m.val_cap = kVals ? static_cast<uint32_t>(val_bytes / 4) : 0xFFFFFFFFu;
           mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(end));
+          if (test_flags(status) & kTestSkipTileCopy) {
+            // test hook: the stage's barrier is armed, no copy is issued
+          } else {
           bulk_g2s(stage, reinterpret_cast<const void*>(oa), static_cast<uint32_t>(off_bytes), &full[s]);
           bulk_g2s(stage + ord_at, reinterpret_cast<const void*>(ra), static_cast<uint32_t>(ord_bytes), &full[s]);
           bulk_g2s(stage + cnt_at, counts + 8ull * tj, 16, &full[s]);
@@ -1027,6 +1030,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
             if constexpr (kVals)
               bulk_g2s(stage + val_at, reinterpret_cast<const void*>(va), static_cast<uint32_t>(val_bytes),
                        &full[s]);
+          }
           }
           }
         }
@@ -1062,7 +1066,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
       } else {
         const unsigned long long now = global_ns();
         if (idle_since == 0) idle_since = now;
-        if (now - idle_since > kWaitLimitNs) {
+        if (now - idle_since > wait_limit_ns(status)) {
           failed = true;
           break;
         }
@@ -1073,7 +1077,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
       atomicOr(status, kStatusTimeout);
       // staged tiles whose work was never published: let their copies land
       // (bounded waits) before the block can exit
-      for (uint32_t x = pushed; x < issued; ++x) (void)mbar_wait(&full[x % kStages], (x / kStages) & 1u);
+      for (uint32_t x = pushed; x < issued; ++x) (void)mbar_wait(&full[x % kStages], (x / kStages) & 1u, status);
     }
     // one stop item per consumer warp
     for (uint32_t i = lane; i < kTileWarps; i += 32) ring[(tail + i) & (kRing - 1)] = kRingDone;
@@ -1089,9 +1093,10 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
     if (lane == 0) {
       const uint32_t pos = atomicAdd(&ring_head, 1u);
       const unsigned long long t0 = global_ns();
+      const unsigned long long limit = wait_limit_ns(status);
       bool ok = true;
       while (ld_acquire_smem(&ring_tail) <= pos) {
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > limit) {
           ok = false;
           break;
         }
@@ -1114,7 +1119,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K, kVals>())
     // Bulk-copy writes are visible to the threads that observe the mbarrier
     // phase, so every lane waits on the stage itself (the phase has completed;
     // the stage cannot move on while this item is outstanding).
-    if (!__all_sync(kFull, mbar_wait(&full[s], (desc >> 16) & 1u))) {
+    if (!__all_sync(kFull, mbar_wait(&full[s], (desc >> 16) & 1u, status))) {
       if (lane == 0) atomicOr(status, kStatusTimeout);
       break;
     }
@@ -1322,7 +1327,7 @@ __global__ void __launch_bounds__(kSyncThreads, sync_min_blocks<K, kVals>())
     }
     issue_failed = ok ? 0 : 1;
     if (!ok)  // let the copies already issued land, then leave
-      for (uint32_t t = 0; t < issued; ++t) (void)mbar_wait(&full[t], 0);
+      for (uint32_t t = 0; t < issued; ++t) (void)mbar_wait(&full[t], 0, status);
   }
   __syncthreads();
   if (issue_failed) return;
@@ -1332,7 +1337,7 @@ __global__ void __launch_bounds__(kSyncThreads, sync_min_blocks<K, kVals>())
   uint32_t i = 0;
   for (; i < my; ++i) {
     const int s = static_cast<int>(i % kStages);
-    const bool ok = mbar_wait(&full[s], (i / kStages) & 1u);
+    const bool ok = mbar_wait(&full[s], (i / kStages) & 1u, status);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -1422,7 +1427,7 @@ __global__ void __launch_bounds__(kSyncThreads, sync_min_blocks<K, kVals>())
     if (failed) {
       atomicOr(status, kStatusTimeout);
       // let staged copies that were issued but not consumed land before exit
-      for (uint32_t t = i; t < issued; ++t) (void)mbar_wait(&full[t % kStages], (t / kStages) & 1u);
+      for (uint32_t t = i; t < issued; ++t) (void)mbar_wait(&full[t % kStages], (t / kStages) & 1u, status);
     }
   }
 }
@@ -1433,7 +1438,7 @@ __global__ void __launch_bounds__(kSyncThreads, sync_min_blocks<K, kVals>())
 // calling warp; called by lane 0, completion counted on `bar`.
 template <class K, bool kVals>
 __device__ __forceinline__ void rss_issue(unsigned char* wbase, int b, uint64_t* bar, const K* keys,
-                                          const uint32_t* vals, uint32_t e0, uint32_t L) {
+                                          const uint32_t* vals, uint32_t e0, uint32_t L, bool skip_copy) {
   using WL = RssWarpLayout<K, kVals>;
   const uintptr_t kb = reinterpret_cast<uintptr_t>(keys);
   const uintptr_t ka = (kb + sizeof(K) * e0) & ~uintptr_t(15);
@@ -1447,6 +1452,7 @@ __device__ __forceinline__ void rss_issue(unsigned char* wbase, int b, uint64_t*
     bytes += static_cast<uint32_t>(vz - va);
   }
   mbar_arrive_expect_tx(bar, bytes);
+  if (skip_copy) return;  // test hook: the barrier is armed, no copy is issued
   bulk_g2s(wbase + WL::kKeys + b * WL::kKeyCap, reinterpret_cast<const void*>(ka), static_cast<uint32_t>(kz - ka),
            bar);
   if constexpr (kVals)
@@ -1481,6 +1487,7 @@ __global__ void __launch_bounds__(kRssThreads, rss_min_blocks<K, kVals>())
   }
   __syncwarp();
   const uint32_t ntiles = plan->bad ? 0u : plan->ntiles;
+  const bool skip_copy = lane == 0 && (test_flags(status) & kTestSkipRssCopy);
   const uint32_t gw = blockIdx.x * kRssWarps + warp;
   const uint32_t W = gridDim.x * kRssWarps;
 
@@ -1499,7 +1506,7 @@ __global__ void __launch_bounds__(kRssThreads, rss_min_blocks<K, kVals>())
     const uint32_t pe0 = __shfl_sync(kFull, q_e0, b), pL = __shfl_sync(kFull, q_L, b);
     // every lane waits itself (bulk-copy data is visible to the lanes that
     // observe the phase); a timeout anywhere fails the whole warp
-    if (!__all_sync(kFull, mbar_wait(&bar[b], (d / kRssBufs) & 1u))) {
+    if (!__all_sync(kFull, mbar_wait(&bar[b], (d / kRssBufs) & 1u, status))) {
       if (lane == 0) atomicOr(status, kStatusTimeout);
       failed = true;
       return;
@@ -1571,7 +1578,7 @@ __global__ void __launch_bounds__(kRssThreads, rss_min_blocks<K, kVals>())
           if (failed) break;
         }
         const int nb = static_cast<int>(issued % kRssBufs);
-        if (lane == 0) rss_issue<K, kVals>(wbase, nb, &bar[nb], keys, vals, ne0, nL);
+        if (lane == 0) rss_issue<K, kVals>(wbase, nb, &bar[nb], keys, vals, ne0, nL, skip_copy);
         if (lane == nb) {
           q_e0 = ne0;
           q_L = nL;
@@ -1585,7 +1592,7 @@ __global__ void __launch_bounds__(kRssThreads, rss_min_blocks<K, kVals>())
   if (lane == 0) {
     // after a failure, let staged copies that were never sorted land (bounded waits)
     if (failed)
-      for (uint32_t x = sorted; x < issued; ++x) (void)mbar_wait(&bar[x % kRssBufs], (x / kRssBufs) & 1u);
+      for (uint32_t x = sorted; x < issued; ++x) (void)mbar_wait(&bar[x % kRssBufs], (x / kRssBufs) & 1u, status);
   }
 }
 

@@ -109,9 +109,15 @@ BatchLayout batch_layout(uint64_t nkeys, uint64_t nseg, uint64_t nreq, int key_b
   return L;
 }
 
+// A slot's batch reports device-detected failures (bad offsets, a bounded
+// wait that ran out, an internal check) through its own control block: the
+// kernels of that batch get `ctl` as their status word, and the word is read
+// back into `hstatus` behind the batch's results.
 struct Slot {
   cudaStream_t stream = nullptr;
   RebaseEntry* htab = nullptr;  // pinned, max_batch_requests entries
+  unsigned char* ctl = nullptr;  // device control block (kDevCtlBytes)
+  unsigned* hstatus = nullptr;   // pinned copy of the batch's status word
   bool busy = false;
 };
 
@@ -127,6 +133,7 @@ struct sn_server {
   sn::RangeArena arena;
   int nslots = 0;
   Slot slots[kMaxSlots];
+  unsigned char* dctl = nullptr;  // the slots' control blocks
 
   std::mutex mu;
   std::condition_variable cv_dispatch, cv_done;
@@ -183,6 +190,12 @@ void CUDART_CB batch_done(void* p) {
   Batch* b = static_cast<Batch*>(p);
   sn_server* s = b->srv;
   const int64_t t = clock_ns();
+  // the batch's device status word, copied back behind its sorts; a bounded
+  // device wait that ran out is a failed batch (SN_ECUDA): SN_ETIMEOUT from
+  // sn_server_wait means "still running"
+  int dev_status = sn::status_from_word(*s->slots[b->slot].hstatus);
+  if (dev_status == SN_ETIMEOUT) dev_status = SN_ECUDA;
+  if (b->status == SN_OK) b->status = dev_status;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     finish_locked(s, b, t);
@@ -223,6 +236,13 @@ cudaError_t issue(sn_server* s, Batch* b, const BatchLayout& L) {
   if ((e = cudaMemcpyAsync(base + L.tab_at, sl.htab, b->reqs.size() * sizeof(RebaseEntry), cudaMemcpyHostToDevice,
                            st)) != cudaSuccess)
     return e;
+  // the batch's control block: the device's wait limit and flags, a clear status word
+  if ((e = cudaMemcpyAsync(sl.ctl, s->dev->status, sn::kDevCtlBytes, cudaMemcpyDeviceToDevice, st)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(sl.ctl, 0, sizeof(unsigned), st)) != cudaSuccess)
+    return e;
+  sn::DeviceInfo di = *s->dev;
+  di.status = reinterpret_cast<unsigned*>(sl.ctl);
   uint32_t* doff = reinterpret_cast<uint32_t*>(base + L.off_at);
   const uint64_t blocks = std::min<uint64_t>((spos + 1 + 255) / 256, 4ull * s->dev->sm_count);
   rebase_offsets_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(doff, spos, static_cast<uint32_t>(kpos), dtab,
@@ -232,12 +252,14 @@ cudaError_t issue(sn_server* s, Batch* b, const BatchLayout& L) {
   if (kb == 4)
     e = sn::launch_segments_u32(reinterpret_cast<uint32_t*>(base + L.keys_at), dvals, doff, spos,
                                 sn::SegMode::kNetworkWarpRss, base + L.scratch_at, L.scratch_bytes, b->tuning, st,
-                                *s->dev);
+                                di);
   else
     e = sn::launch_segments_u64(reinterpret_cast<uint64_t*>(base + L.keys_at), dvals, doff, spos,
                                 sn::SegMode::kNetworkWarpRss, base + L.scratch_at, L.scratch_bytes, b->tuning, st,
-                                *s->dev);
+                                di);
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(sl.hstatus, sl.ctl, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
   kpos = 0;
   for (const Request& r : b->reqs) {
     if (r.nkeys) {
@@ -332,7 +354,9 @@ void destroy_resources(sn_server* s) {
   for (int i = 0; i < s->nslots; ++i) {
     if (s->slots[i].stream) cudaStreamDestroy(s->slots[i].stream);
     if (s->slots[i].htab) cudaFreeHost(s->slots[i].htab);
+    if (s->slots[i].hstatus) cudaFreeHost(s->slots[i].hstatus);
   }
+  if (s->dctl) cudaFree(s->dctl);
   if (s->dbuf) cudaFree(s->dbuf);
 }
 
@@ -371,10 +395,20 @@ int sn_server_create(const sn_server_config* cfg, sn_server** out) {
   }
   s->arena.reset(c.budget_bytes);
   s->nslots = c.slots;
+  if (cudaMalloc(&s->dctl, kMaxSlots * sn::kDevCtlBytes) != cudaSuccess) {
+    cudaGetLastError();
+    s->dctl = nullptr;
+    destroy_resources(s);
+    delete s;
+    return SN_ENOMEM;
+  }
   for (int i = 0; i < c.slots; ++i) {
+    s->slots[i].ctl = s->dctl + i * sn::kDevCtlBytes;
     if (cudaStreamCreateWithFlags(&s->slots[i].stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaHostAlloc(reinterpret_cast<void**>(&s->slots[i].htab), c.max_batch_requests * sizeof(RebaseEntry),
-                      cudaHostAllocDefault) != cudaSuccess) {
+                      cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&s->slots[i].hstatus), sizeof(unsigned), cudaHostAllocDefault) !=
+            cudaSuccess) {
       cudaGetLastError();
       destroy_resources(s);
       delete s;
@@ -435,12 +469,17 @@ int sn_server_wait(sn_server* srv, uint64_t ticket, int64_t timeout_ns) {
   std::unique_lock<std::mutex> lk(srv->mu);
   auto it = srv->state.find(ticket);
   if (it == srv->state.end()) return SN_EINVAL;
-  auto done = [&] { return srv->state[ticket] != kRunning; };
+  // done, or gone: another thread waiting on the same ticket collected it
+  auto done = [&] {
+    const auto f = srv->state.find(ticket);
+    return f == srv->state.end() || f->second != kRunning;
+  };
   if (timeout_ns < 0)
     srv->cv_done.wait(lk, done);
   else if (timeout_ns > 0)
     srv->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), done);
   it = srv->state.find(ticket);
+  if (it == srv->state.end()) return SN_EINVAL;
   if (it->second == kRunning) return SN_ETIMEOUT;
   const int st = it->second;
   srv->state.erase(it);

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "smallsort.h"
 #include "sn_internal.h"
@@ -317,3 +318,85 @@ int sn_tuning_load(const char* path) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// sn_tune: load a saved parameter table, or tune every key type and payload
+// kind on a built-in synthetic batch.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// SplitMix64 (Steele, Lea, Flood 2014): the synthetic batch's random numbers.
+uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Tunes (key_bytes, payload) on 2^20 segments with geometric(0.15) lengths
+// capped at 256 (the shape of the library's uneven-batch workload), keys
+// uniform, built on the host and copied to the device.
+int tune_synthetic(int key_bytes, bool with_vals) {
+  constexpr uint64_t kSeg = 1ull << 20;
+  uint64_t rng = 0x5EEDull + key_bytes * 2 + (with_vals ? 1 : 0);
+  std::vector<uint32_t> off(kSeg + 1);
+  off[0] = 0;
+  for (uint64_t i = 0; i < kSeg; ++i) {
+    uint32_t len = 1;  // geometric on {1, 2, ...}: P(len = k) = 0.15 * 0.85^(k-1)
+    while (len < SN_MAX_SEGMENT && (splitmix(rng) >> 11) * (1.0 / 9007199254740992.0) >= 0.15) ++len;
+    off[i + 1] = off[i] + len;
+  }
+  const uint64_t nk = off[kSeg];
+  std::vector<uint64_t> keys(nk);
+  for (auto& k : keys) k = splitmix(rng);
+  std::vector<uint32_t> vals;
+  if (with_vals) {
+    vals.resize(nk);
+    for (uint64_t i = 0; i < nk; ++i) vals[i] = static_cast<uint32_t>(i);
+  }
+  void *dk = nullptr, *dv = nullptr, *doff = nullptr;
+  int rc = SN_OK;
+  if (cudaMalloc(&dk, nk * key_bytes) != cudaSuccess || cudaMalloc(&doff, (kSeg + 1) * 4) != cudaSuccess ||
+      (with_vals && cudaMalloc(&dv, nk * 4) != cudaSuccess)) {
+    cudaGetLastError();
+    rc = SN_ENOMEM;
+  }
+  if (rc == SN_OK) {
+    bool ok = cudaMemcpy(doff, off.data(), (kSeg + 1) * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (key_bytes == 8) {
+      ok = ok && cudaMemcpy(dk, keys.data(), nk * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    } else {
+      std::vector<uint32_t> k32(nk);
+      for (uint64_t i = 0; i < nk; ++i) k32[i] = static_cast<uint32_t>(keys[i] >> 32);
+      ok = ok && cudaMemcpy(dk, k32.data(), nk * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (with_vals) ok = ok && cudaMemcpy(dv, vals.data(), nk * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    rc = ok ? sn_tune_segments(dk, static_cast<uint32_t*>(dv), static_cast<const uint32_t*>(doff), kSeg, key_bytes,
+                               nullptr, nullptr, nullptr)
+            : SN_ECUDA;
+  }
+  if (dk) cudaFree(dk);
+  if (dv) cudaFree(dv);
+  if (doff) cudaFree(doff);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int sn_tune(const char* path) {
+  if (path != nullptr) {
+    if (FILE* f = std::fopen(path, "r")) {
+      std::fclose(f);
+      return sn_tuning_load(path);
+    }
+  }
+  int err = SN_OK;
+  if (sn::device_info(&err) == nullptr) return err;
+  for (int kb : {4, 8})
+    for (bool v : {false, true}) {
+      const int rc = tune_synthetic(kb, v);
+      if (rc != SN_OK) return rc;
+    }
+  return path != nullptr ? sn_tuning_save(path) : SN_OK;
+}

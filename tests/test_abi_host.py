@@ -31,7 +31,8 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("sn_sort_fixed", "sn_sort_segments", "rss_sort_segments", "sn_check",
+    for required in ("sn_sort_fixed", "sn_sort_fixed_u64", "sn_sort_segments", "sn_sort_segments_u64",
+                     "rss_sort_segments", "rss_sort_segments_u64", "sn_get_last_cuda_error", "sn_tune", "sn_check",
                      "sn_status_string"):
         assert required in names
 

@@ -127,3 +127,27 @@ def test_synchronous_tile_mode_many_tiles(dtype, with_vals, lengths, lo, hi, res
             assert np.array_equal(to_host(dk, dtype), ek)
             if with_vals:
                 assert np.array_equal(to_host(dv, np.uint32), ev)
+
+
+def test_sn_tune_tunes_saves_and_loads(tmp_path, restore_defaults):
+    # sn_tune(path): with no file, tunes the four key type / payload kinds on
+    # the library's synthetic batch, installs them and writes the file; with
+    # the file, loads it.  The sets it chose sort like any other.
+    path = str(tmp_path / "tuned.txt")
+    assert sn.sn_tune(path) == sn.SN_OK
+    chosen = {(kb, v): sn.sn_tuning_get(kb, v) for kb in (4, 8) for v in (False, True)}
+    assert open(path).read().startswith("smallsort-tuning")
+    for kb in (4, 8):
+        for v in (False, True):
+            sn.check(sn.sn_tuning_set(kb, v), "reset")
+    assert sn.sn_tune(path) == sn.SN_OK  # the file now exists: a load
+    assert {(kb, v): sn.sn_tuning_get(kb, v) for kb in (4, 8) for v in (False, True)} == chosen
+    k, v, off = wl.segment_batch(40_000, "geometric", "fewdistinct", np.uint64, True, seed=82, p=0.15, cap=256)
+    ek, ev = oracle.sort_segments(k, v, off)
+    dk, dv = to_dev(k), to_dev(v)
+    sn.check(sn.sn_sort_segments_u64(dk, dv, to_dev(off)), "sort")
+    assert sn.sn_get_last_cuda_error() == sn.SN_OK
+    assert np.array_equal(to_host(dk, np.uint64), ek) and np.array_equal(to_host(dv, np.uint32), ev)
+    bad = tmp_path / "bad.txt"
+    bad.write_text("not a tuning file\n")
+    assert sn.sn_tune(str(bad)) == sn.SN_EINVAL

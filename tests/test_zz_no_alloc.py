@@ -5,14 +5,15 @@ memory when they sort (a fixed budget reserved up front, a thread that must
 not enter the allocator).  Its scratch is a fixed array inside the library
 that every call reuses, so this test runs it twice in a row on different
 batches and checks each result bit for bit against sn_sort_segments_u64 on a
-copy of the same input.  It also checks the size limit.  The file name makes
-pytest collect it last.
+copy of the same input, and against the CPU oracle's per-segment stable sort.
+It also checks the size limit.  The file name makes pytest collect it last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_2002_05599_gb300 as sn
 from paper_2002_05599_gb300 import workloads as wl
 from gpu_util import to_dev, to_host
@@ -49,6 +50,9 @@ def test_noalloc_matches_allocating_entry_point_twice():
         assert sn.sn_check() == sn.SN_OK
         assert np.array_equal(to_host(got_k, np.uint64), to_host(ref_k, np.uint64))
         assert np.array_equal(to_host(got_v, np.uint32), to_host(ref_v, np.uint32))
+        ek, ev = oracle.sort_segments(k, v, off)  # element by element against the oracle
+        assert np.array_equal(to_host(got_k, np.uint64), ek)
+        assert np.array_equal(to_host(got_v, np.uint32), ev)
         # keys only
         got_k2 = to_dev(k)
         assert lib.sn_sort_segments_u64_noalloc(got_k2.data_ptr(), None, d_off.data_ptr(), nseg, stream) == 0
