@@ -65,7 +65,7 @@ int sn_sort_fixed_u64(uint64_t *keys, int n, uint64_t count, sn_stream_t stream)
 
 /*
  * Network families for the fixed-size calls (Sec. 2.2.1): the best known
- * networks (sizes 1, 3, 5, 9, 12, 16, 19, 25, 29, 35, 39, 46, 51, 56, 60 for
+ * networks (sizes 1, 3, 5, 9, 12, 16, 19, 25, 29, 35, 39, 45, 51, 56, 60 for
  * n = 2..16), or Bose and Nelson's recursive construction (BN-L of the paper:
  * 65 comparators at n = 16).  Both sort every input; they differ in size,
  * depth and locality only.

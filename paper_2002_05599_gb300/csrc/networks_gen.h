@@ -35,7 +35,7 @@
 #define SN_NET_SIZE_8 19
 #define SN_NET_8(CE) CE(0,1) CE(2,3) CE(0,2) CE(1,3) CE(1,2) CE(4,5) CE(6,7) CE(4,6) CE(5,7) CE(5,6) CE(0,4) CE(2,6) CE(2,4) CE(1,5) CE(3,7) CE(3,5) CE(1,2) CE(3,4) CE(5,6)
 
-/* n=9: 25 comparators, depth 8, from searched12-bottom-bottom-bottom */
+/* n=9: 25 comparators, depth 8, from search(prefix=levels<=5 of the chosen n=12 network, restarts=2000, seed=1)-bottom-bottom-bottom */
 #define SN_NET_SIZE_9 25
 #define SN_NET_9(CE) CE(1,2) CE(3,4) CE(5,6) CE(7,8) CE(1,3) CE(5,7) CE(2,4) CE(6,8) CE(0,4) CE(0,8) CE(2,7) CE(3,6) CE(4,8) CE(1,5) CE(2,3) CE(6,7) CE(0,5) CE(5,6) CE(4,7) CE(3,5) CE(4,6) CE(0,2) CE(0,1) CE(4,5) CE(2,3)
 
@@ -43,17 +43,17 @@
 #define SN_NET_SIZE_10 29
 #define SN_NET_10(CE) CE(4,9) CE(3,8) CE(2,7) CE(1,6) CE(0,5) CE(1,4) CE(6,9) CE(0,3) CE(5,8) CE(0,2) CE(3,6) CE(7,9) CE(0,1) CE(2,4) CE(5,7) CE(8,9) CE(1,2) CE(4,6) CE(7,8) CE(3,5) CE(2,5) CE(6,8) CE(1,3) CE(4,7) CE(2,3) CE(6,7) CE(3,4) CE(5,6) CE(4,5)
 
-/* n=11: 35 comparators, depth 9, from searched12-top */
+/* n=11: 35 comparators, depth 9, from search(prefix=levels<=5 of the chosen n=12 network, restarts=2000, seed=1)-top */
 #define SN_NET_SIZE_11 35
 #define SN_NET_11(CE) CE(0,1) CE(2,3) CE(4,5) CE(6,7) CE(8,9) CE(0,2) CE(4,6) CE(8,10) CE(1,3) CE(5,7) CE(0,4) CE(1,5) CE(2,6) CE(3,7) CE(0,8) CE(1,9) CE(2,10) CE(5,10) CE(6,9) CE(1,2) CE(4,8) CE(5,6) CE(9,10) CE(3,8) CE(2,3) CE(8,9) CE(1,4) CE(7,10) CE(6,8) CE(7,9) CE(3,5) CE(2,4) CE(3,4) CE(7,8) CE(5,6)
 
-/* n=12: 39 comparators, depth 9, from searched12 */
+/* n=12: 39 comparators, depth 9, from search(prefix=levels<=5 of the chosen n=12 network, restarts=2000, seed=1) */
 #define SN_NET_SIZE_12 39
 #define SN_NET_12(CE) CE(0,1) CE(2,3) CE(4,5) CE(6,7) CE(8,9) CE(10,11) CE(0,2) CE(4,6) CE(8,10) CE(1,3) CE(5,7) CE(9,11) CE(0,4) CE(1,5) CE(2,6) CE(3,7) CE(0,8) CE(1,9) CE(2,10) CE(3,11) CE(5,10) CE(6,9) CE(7,11) CE(1,2) CE(4,8) CE(5,6) CE(9,10) CE(3,8) CE(2,3) CE(8,9) CE(1,4) CE(7,10) CE(6,8) CE(7,9) CE(3,5) CE(2,4) CE(3,4) CE(7,8) CE(5,6)
 
-/* n=13: 46 comparators, depth 10, from paper16-top-top-top */
-#define SN_NET_SIZE_13 46
-#define SN_NET_13(CE) CE(0,1) CE(2,3) CE(4,5) CE(6,7) CE(8,9) CE(10,11) CE(0,2) CE(4,6) CE(8,10) CE(1,3) CE(5,7) CE(9,11) CE(0,4) CE(8,12) CE(1,5) CE(2,6) CE(3,7) CE(0,8) CE(1,9) CE(2,10) CE(3,11) CE(4,12) CE(5,10) CE(6,9) CE(3,12) CE(7,11) CE(1,2) CE(4,8) CE(1,4) CE(2,8) CE(2,4) CE(5,6) CE(9,10) CE(3,8) CE(7,12) CE(6,8) CE(10,12) CE(3,5) CE(7,9) CE(3,4) CE(5,6) CE(7,8) CE(9,10) CE(11,12) CE(6,7) CE(8,9)
+/* n=13: 45 comparators, depth 10, from evolve(n=13, target=45, seed=35, reflection, prefix=(0,1)(2,3)(4,5)(7,8)(9,10)(11,12), EVOLVE_RANDOM=40, EVOLVE_WORSE=20) */
+#define SN_NET_SIZE_13 45
+#define SN_NET_13(CE) CE(0,1) CE(2,3) CE(4,5) CE(7,8) CE(9,10) CE(11,12) CE(3,10) CE(2,9) CE(5,8) CE(0,11) CE(4,7) CE(1,12) CE(0,2) CE(1,5) CE(6,8) CE(10,12) CE(8,12) CE(6,10) CE(4,6) CE(0,4) CE(7,11) CE(2,6) CE(9,11) CE(1,9) CE(3,5) CE(5,8) CE(3,7) CE(2,4) CE(1,3) CE(6,9) CE(10,11) CE(5,10) CE(8,11) CE(5,7) CE(7,9) CE(1,2) CE(3,4) CE(5,6) CE(8,10) CE(8,9) CE(6,7) CE(2,3) CE(4,5) CE(5,6) CE(3,4)
 
 /* n=14: 51 comparators, depth 10, from paper16-top-top */
 #define SN_NET_SIZE_14 51

@@ -175,7 +175,8 @@ int large_entry(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg,
 namespace sn {
 
 size_t segments_scratch_bytes(uint64_t nseg, const SegTuning& t) {
-  return seg::ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total;
+  // the window kernel (tile_mode 2) needs only the validation word
+  return t.tile_mode == 2 ? 256 : seg::ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total;
 }
 
 }  // namespace sn
@@ -348,7 +349,7 @@ const char* sn_status_string(int status) {
 // nothing.  The kernels are the ones sn_sort_segments_u64 runs.
 // ---------------------------------------------------------------------------
 
-#include "sn_segments.cuh"
+#include "sn_window.cuh"
 
 namespace sn {
 namespace {

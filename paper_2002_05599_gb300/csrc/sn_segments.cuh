@@ -166,6 +166,9 @@ template <> struct RssMem<uint32_t, true> {
       : buf(reinterpret_cast<uint64_t*>(p)), cnt(reinterpret_cast<uint32_t*>(p + 256 * 8)) {}
   __device__ __forceinline__ uint64_t get(int i) const { return buf[i]; }
   __device__ __forceinline__ void set(int i, uint64_t v) const { buf[i] = v; }
+  // slot i as a parking place for a payload word (in-place write-back)
+  __device__ __forceinline__ void stash(int i, uint32_t v) const { buf[i] = v; }
+  __device__ __forceinline__ uint32_t unstash(int i) const { return static_cast<uint32_t>(buf[i]); }
 };
 template <> struct RssMem<uint64_t, true> {
   static constexpr size_t kBytes = 256 * 8 + 256 * 2 + kRssMaxBuckets * 4;
@@ -180,6 +183,8 @@ template <> struct RssMem<uint64_t, true> {
     key[i] = v.key;
     idx[i] = static_cast<uint16_t>(v.idx);
   }
+  __device__ __forceinline__ void stash(int i, uint32_t v) const { key[i] = v; }
+  __device__ __forceinline__ uint32_t unstash(int i) const { return static_cast<uint32_t>(key[i]); }
 };
 
 // Per-warp region of the RSS kernel: kRssBufs staging buffers (keys, payload)
@@ -582,9 +587,12 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K, kVals>& rm, in
 // one 64-bit word (one min/max orders both), 8-byte keys ordered by key first
 // and, only when equal keys end out of position order somewhere, once more
 // by (key, position).
-template <class K, bool kVals, bool kF>
+// kInPlace: gk / gv point into the staged copy itself (the results replace
+// the segment where it is staged), so every lane gathers its payload before
+// any lane writes.
+template <class K, bool kVals, bool kF, bool kInPlace = false>
 __device__ __forceinline__ void net64_segment(const K* kbuf, const uint32_t* vbuf, int p, int pv, int L, int lane,
-                                              K* __restrict__ gk, uint32_t* __restrict__ gv) {
+                                              K* gk, uint32_t* gv) {
   const int e1 = 32 + lane;
   constexpr K kTop = static_cast<K>(~static_cast<K>(0));
   if constexpr (kVals && sizeof(K) == 8) {
@@ -604,13 +612,15 @@ __device__ __forceinline__ void net64_segment(const K* kbuf, const uint32_t* vbu
       lo = KeyIdx<K>{FI::key(a), FI::idx(a)};
       hi = KeyIdx<K>{FI::key(b), FI::idx(b)};
     }
+    const uint32_t vlo = lane < L ? vbuf[pv + lo.ix] : 0u, vhi = e1 < L ? vbuf[pv + hi.ix] : 0u;
+    if constexpr (kInPlace) __syncwarp();
     if (lane < L) {
       gk[lane] = key_dec<K, kF>(lo.k);
-      gv[lane] = vbuf[pv + lo.ix];
+      gv[lane] = vlo;
     }
     if (e1 < L) {
       gk[e1] = key_dec<K, kF>(hi.k);
-      gv[e1] = vbuf[pv + hi.ix];
+      gv[e1] = vhi;
     }
   } else {
     using IO = RssIO<K, kVals>;
@@ -620,13 +630,19 @@ __device__ __forceinline__ void net64_segment(const K* kbuf, const uint32_t* vbu
     It hi = e1 < L ? IO::make(key_enc<K, kF>(kbuf[p + e1]), static_cast<uint32_t>(e1))
                    : IO::sentinel(static_cast<uint32_t>(e1));
     warp_sort64(lo, hi, lane);
+    uint32_t vlo = 0, vhi = 0;
+    if constexpr (kVals) {
+      if (lane < L) vlo = vbuf[pv + IO::idx(lo)];
+      if (e1 < L) vhi = vbuf[pv + IO::idx(hi)];
+    }
+    if constexpr (kInPlace) __syncwarp();
     if (lane < L) {
       gk[lane] = key_dec<K, kF>(IO::key(lo));
-      if constexpr (kVals) gv[lane] = vbuf[pv + IO::idx(lo)];
+      if constexpr (kVals) gv[lane] = vlo;
     }
     if (e1 < L) {
       gk[e1] = key_dec<K, kF>(IO::key(hi));
-      if constexpr (kVals) gv[e1] = vbuf[pv + IO::idx(hi)];
+      if constexpr (kVals) gv[e1] = vhi;
     }
   }
 }
@@ -652,10 +668,13 @@ __device__ __forceinline__ void net64_segment(const K* kbuf, const uint32_t* vbu
 //     (rare unless keys repeat) are sorted by the whole warp (32-lane network,
 //     or a bitonic pass in shared memory above 32);
 //  7. write back (payload gathered by original position).
-template <class K, bool kVals, bool kF>
+//  kInPlace: gk / gv point into the staged copy itself; the payload words are
+//  then parked in the item buffer first and written once every lane has
+//  gathered its own.
+template <class K, bool kVals, bool kF, bool kInPlace = false>
 __device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf, int p, int pv, int L,
-                                            const RssMem<K, kVals>& rm, int lane, int two_min,
-                                            K* __restrict__ gk, uint32_t* __restrict__ gv) {
+                                            const RssMem<K, kVals>& rm, int lane, int two_min, K* gk,
+                                            uint32_t* gv) {
   using IO = RssIO<K, kVals>;
   using It = typename IO::T;
   constexpr K kTop = static_cast<K>(~static_cast<K>(0));
@@ -811,13 +830,31 @@ __device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf,
   // 7. write the sorted segment straight to its place in global memory
   //    (coalesced: lane l writes items 32 r + l; payload gathered by
   //    original position from the staged copy)
+  if constexpr (kInPlace && kVals) {
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int e = (r << 5) + lane;
-    if (r < rounds && e < L) {
-      const It y = rm.get(e);
-      gk[e] = key_dec<K, kF>(IO::key(y));
-      if constexpr (kVals) gv[e] = vbuf[pv + IO::idx(y)];
+    for (int r = 0; r < 8; ++r) {
+      const int e = (r << 5) + lane;
+      if (r < rounds && e < L) {
+        const It y = rm.get(e);
+        gk[e] = key_dec<K, kF>(IO::key(y));
+        rm.stash(e, vbuf[pv + IO::idx(y)]);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = (r << 5) + lane;
+      if (r < rounds && e < L) gv[e] = rm.unstash(e);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = (r << 5) + lane;
+      if (r < rounds && e < L) {
+        const It y = rm.get(e);
+        gk[e] = key_dec<K, kF>(IO::key(y));
+        if constexpr (kVals) gv[e] = vbuf[pv + IO::idx(y)];
+      }
     }
   }
   __syncwarp();
@@ -1729,22 +1766,6 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
-}
-
-template <class K, bool kF = false>
-cudaError_t launch_segments(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, SegMode mode,
-                            void* scratch, size_t scratch_bytes, const SegTuning& t, cudaStream_t s,
-                            const DeviceInfo& d) {
-  if (t.tile_units < 512 || t.rss_two_min < 16 || t.rss_two_min > kMaxSeg || t.net_classes > 0x1Fu ||
-      t.tile_mode < 0 || t.tile_mode > 1)
-    return cudaErrorInvalidValue;
-  if (!(vals ? tile_fits<K, true>(t.tile_units, t.tile_stages, t.tile_mode)
-             : tile_fits<K, false>(t.tile_units, t.tile_stages, t.tile_mode)))
-    return cudaErrorInvalidValue;
-  if (scratch_bytes < ScratchLayout(nseg, static_cast<uint32_t>(t.tile_units)).total) return cudaErrorInvalidValue;
-  const bool rss = mode == SegMode::kRssOnly;
-  return vals ? launch_all<K, true, kF>(keys, vals, offsets, nseg, rss, scratch, t, s, d)
-              : launch_all<K, false, kF>(keys, vals, offsets, nseg, rss, scratch, t, s, d);
 }
 
 }  // namespace

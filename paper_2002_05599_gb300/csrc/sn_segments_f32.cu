@@ -1,6 +1,6 @@
 // Segmented sorting, f32 keys (IEEE-754 totalOrder through the order-preserving
 // code of key_enc): instantiation unit (kernels in sn_segments.cuh).
-#include "sn_segments.cuh"
+#include "sn_window.cuh"
 
 namespace sn {
 

@@ -1,5 +1,5 @@
 // Segmented sorting, uint32_t keys: instantiation unit (kernels in sn_segments.cuh).
-#include "sn_segments.cuh"
+#include "sn_window.cuh"
 
 namespace sn {
 
@@ -10,8 +10,8 @@ cudaError_t launch_segments_u32(uint32_t* keys, uint32_t* vals, const uint32_t* 
 }
 
 bool tile_fits_u32(bool vals, int tile_units, int stages, int mode) {
-  return vals ? seg::tile_fits<uint32_t, true>(tile_units, stages, mode)
-              : seg::tile_fits<uint32_t, false>(tile_units, stages, mode);
+  return vals ? seg::seg_fits<uint32_t, true>(tile_units, stages, mode)
+              : seg::seg_fits<uint32_t, false>(tile_units, stages, mode);
 }
 
 }  // namespace sn

@@ -1,5 +1,5 @@
 // Segmented sorting, uint64_t keys: instantiation unit (kernels in sn_segments.cuh).
-#include "sn_segments.cuh"
+#include "sn_window.cuh"
 
 namespace sn {
 
@@ -10,8 +10,8 @@ cudaError_t launch_segments_u64(uint64_t* keys, uint32_t* vals, const uint32_t* 
 }
 
 bool tile_fits_u64(bool vals, int tile_units, int stages, int mode) {
-  return vals ? seg::tile_fits<uint64_t, true>(tile_units, stages, mode)
-              : seg::tile_fits<uint64_t, false>(tile_units, stages, mode);
+  return vals ? seg::seg_fits<uint64_t, true>(tile_units, stages, mode)
+              : seg::seg_fits<uint64_t, false>(tile_units, stages, mode);
 }
 
 }  // namespace sn

@@ -32,7 +32,7 @@ bool g_touched[kDevs][2][2];
 bool tuning_valid(const SegTuning& t) {
   return t.tile_units >= 512 && t.tile_units <= 16384 && t.net_classes <= 0x1Fu && t.rss_two_min >= 16 &&
          t.rss_two_min <= SN_MAX_SEGMENT && t.tile_stages >= 2 && t.tile_stages <= 4 && t.tile_mode >= 0 &&
-         t.tile_mode <= 1;
+         t.tile_mode <= 2;
 }
 
 SegTuning current_tuning(int device, int key_bytes, bool vals) {

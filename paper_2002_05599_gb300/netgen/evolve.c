@@ -17,7 +17,13 @@
  *      pair with the largest reduction of |S| (ties at random, now and then a
  *      random pair among those that move something);
  *   4. keep the copy if it is no longer than the current suffix (equal length
- *      is kept too, so the search can drift across plateaus).
+ *      is kept too, so the search can drift across plateaus), and now and
+ *      then one a comparator longer; after many steps without a new best the
+ *      search goes back to the best network found.
+ * Environment: EVOLVE_RANDOM (percent of completion steps that pick a random
+ * useful pair, default 6), EVOLVE_WORSE (per mille of one-longer copies kept,
+ * default 20), EVOLVE_RESTART (steps without a new best before going back,
+ * default 2e6).
  * With the reflection flag every change is applied to a comparator and to its
  * mirror image (n-1-j, n-1-i) together, which keeps the network symmetric
  * under reversing the channels and complementing the bits; the search space
@@ -51,6 +57,7 @@ typedef struct {
 } Cmp;
 
 static int n, sym;
+static int random_pct = 6; /* share of completion steps that take a random useful pair */
 static uint32_t *pre_set, pre_size; /* output set of the prefix */
 static uint32_t *work;              /* current set */
 static uint32_t work_size;
@@ -145,7 +152,7 @@ static int complete(Cmp *s, int m)
             }
         if (nc == 0) break;
         int pick;
-        if ((rng_next() & 15u) == 0) {
+        if (rnd(100) < (uint32_t)random_pct) {
             pick = (int)rnd((uint32_t)nc);
         } else {
             int list[MAXN * MAXN], nl = 0;
@@ -210,7 +217,22 @@ static void drop(Cmp *s, int *m, int k)
 static void mutate(Cmp *s, int *m)
 {
     if (*m == 0) return;
-    switch (rnd(6)) {
+    switch (rnd(8)) {
+    case 6: { /* move one comparator to another position */
+        int k = (int)rnd((uint32_t)*m), to = (int)rnd((uint32_t)*m);
+        Cmp c = s[k];
+        remove_at(s, m, k);
+        insert_at(s, m, to <= *m ? to : *m, c);
+        break;
+    }
+    case 7: { /* shift one end of a comparator to a neighbouring channel */
+        int k = (int)rnd((uint32_t)*m);
+        Cmp c = s[k];
+        int d = (rng_next() & 1) ? 1 : -1;
+        if (rng_next() & 1) c.i = (uint8_t)(c.i + d); else c.j = (uint8_t)(c.j + d);
+        if (c.i < c.j && c.j < n && c.i < 200) s[k] = c;
+        break;
+    }
     case 0: /* drop one */
     case 1:
         drop(s, m, (int)rnd((uint32_t)*m));
@@ -283,12 +305,20 @@ int main(int argc, char **argv)
     Cmp cur[MAXC], cand[MAXC];
     int cur_m = complete(cur, (load_prefix_set(), 0));
     cur_m = evaluate(cur, cur_m);
-    int best = MAXC + 1;
+    int best = MAXC + 1, best_m = -1;
+    Cmp best_net[MAXC];
+    unsigned long long since_best = 0;
+    const char *env;
+    unsigned worse_permille = (env = getenv("EVOLVE_WORSE")) ? (unsigned)atoi(env) : 20;
+    unsigned long long restart_after = (env = getenv("EVOLVE_RESTART")) ? strtoull(env, NULL, 10) : 2000000ull;
+    if ((env = getenv("EVOLVE_RANDOM"))) random_pct = atoi(env);
     const clock_t t0 = clock();
     unsigned long long iters = 0;
     for (;;) {
         if (npre + cur_m < best) {
             best = npre + cur_m;
+            best_m = cur_m;
+            memcpy(best_net, cur, sizeof(Cmp) * (size_t)cur_m);
             printf("size %d\n", best);
             for (int c = 0; c < npre; ++c) printf("%d %d\n", pre[c].i, pre[c].j);
             for (int c = 0; c < cur_m; ++c) printf("%d %d\n", cur[c].i, cur[c].j);
@@ -302,9 +332,18 @@ int main(int argc, char **argv)
         m = evaluate(cand, m);
         m = complete(cand, m);
         if (work_size != (uint32_t)n + 1) continue;
-        if (m <= cur_m) {
+        /* equal or shorter: always; one longer: now and then (leaves plateaus);
+           after many steps without a new best, restart from the best */
+        if (m <= cur_m || (m == cur_m + 1 && rnd(1000) < (uint32_t)worse_permille)) {
             cur_m = m;
             memcpy(cur, cand, sizeof(Cmp) * (size_t)m);
+        }
+        if (npre + cur_m < best) {
+            since_best = 0;
+        } else if (++since_best > restart_after && best_m >= 0) {
+            cur_m = best_m;
+            memcpy(cur, best_net, sizeof(Cmp) * (size_t)best_m);
+            since_best = 0;
         }
     }
     fprintf(stderr, "iterations %llu, best %d\n", iters, best);

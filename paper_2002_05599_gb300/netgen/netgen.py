@@ -18,8 +18,10 @@ Where the networks come from:
   sentinel meets and untangling the reversed comparators this leaves (Knuth,
   TAOCP vol. 3, Sec. 5.3.4, exercise 16);
 * n = 8: Batcher's odd-even merge sort (19 comparators);
-* n = 11..13: the best of pruning and the randomised greedy search in
-  ``search.c`` (results stored in ``searched.json`` with the seed that made them);
+* n = 11..13: the best of pruning, the randomised greedy search in
+  ``search.c`` and the evolutionary search in ``evolve.c`` (results stored in
+  ``searched.json`` with the arguments that reproduce them; n = 13 from
+  ``evolve.c``, 45 comparators);
 * the warp network for 17..32 items: Batcher's bitonic sorter written with
   ascending comparators only (the first step of each merge compares mirrored
   positions, partner ``i ^ (k - 1)``; later steps use ``i ^ j``).
@@ -269,7 +271,7 @@ def pruned_candidates():
     frontier = [(16, PAPER_BEST16, "paper16"), (10, PAPER_OPT10, "paper10"),
                 (8, batcher_odd_even(8), "batcher-odd-even")]
     for rec in _searched():
-        frontier.append((rec["n"], [tuple(p) for p in rec["pairs"]], f"searched{rec['n']}"))
+        frontier.append((rec["n"], [tuple(p) for p in rec["pairs"]], rec["provenance"]))
     while frontier:
         nxt = []
         for n, net, prov in frontier:
@@ -427,6 +429,35 @@ def search(n: int, restarts: int, seeds, prefix_levels=None) -> None:
         print("improved:", found["provenance"], best)
 
 
+def evolve(n: int, target: int, seed: int, seconds: float, reflection: bool, prefix, env=None) -> bool:
+    """Run evolve.c (deterministic for a seed: it stops at the target size) and
+    store a network smaller than the chosen one in searched.json."""
+    exe = os.path.join(HERE, "_evolve")
+    subprocess.check_call(["gcc", "-O3", "-o", exe, os.path.join(HERE, "evolve.c")])
+    args = [exe, str(n), str(target), str(seed), str(seconds), "1" if reflection else "0"]
+    args += [str(x) for p in prefix for x in p]
+    run_env = dict(os.environ, **{k: str(v) for k, v in (env or {}).items()})
+    out = subprocess.run(args, capture_output=True, text=True, env=run_env).stdout.split("\n")
+    heads = [k for k, ln in enumerate(out) if ln.startswith("size ")]
+    if not heads:
+        return False
+    size = int(out[heads[-1]].split()[1])
+    pairs = [tuple(int(x) for x in ln.split()) for ln in out[heads[-1] + 1:heads[-1] + 1 + size]]
+    if size >= len(choose_networks()[n]["pairs"]) or not sorts_all_01(n, pairs):
+        return False
+    knobs = ", ".join(f"{k}={v}" for k, v in (env or {}).items())
+    pre = "".join(f"({i},{j})" for i, j in prefix)
+    recs = [r for r in _searched() if r["n"] != n]
+    recs.append({"n": n, "pairs": [list(p) for p in pairs],
+                 "provenance": f"evolve(n={n}, target={target}, seed={seed}"
+                               f"{', reflection' if reflection else ''}, prefix={pre}{', ' + knobs if knobs else ''})"})
+    with open(SEARCHED, "w") as f:
+        json.dump(recs, f, indent=1)
+        f.write("\n")
+    print(f"n={n}: {size} comparators from evolve.c")
+    return True
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--check", action="store_true", help="fail if the outputs are stale")
@@ -434,7 +465,13 @@ def main(argv=None) -> int:
     ap.add_argument("--restarts", type=int, default=200)
     ap.add_argument("--seeds", type=int, nargs="*", default=[1, 2, 3])
     ap.add_argument("--levels", type=int, nargs="*", default=None)
+    ap.add_argument("--evolve13", action="store_true",
+                    help="rerun the evolutionary search that found the 45-comparator n=13 network")
     args = ap.parse_args(argv)
+    if args.evolve13:
+        evolve(13, 45, 35, 3600, True, [(0, 1), (2, 3), (4, 5), (7, 8), (9, 10), (11, 12)],
+               {"EVOLVE_RANDOM": 40, "EVOLVE_WORSE": 20})
+        return 0
     if args.search:
         search(args.search, args.restarts, args.seeds, args.levels)
         return 0

@@ -140,6 +140,11 @@ def test_tile_shape_limits(lib):
     for kb, v in ((4, 1), (8, 0), (8, 1)):
         assert not fits(kb, v, 8192, 2, 1) and fits(kb, v, 4096, 2, 1)
     assert not fits(4, 0, 32768, 2) and not fits(4, 0, 256, 2)
+    # window kernel (mode 2): four warps a block, each with `stages` windows of
+    # tile_units items (key + payload bytes each) plus its sample-sort scratch
+    assert fits(4, 0, 4096, 3, 2) and not fits(4, 0, 4096, 4, 2)   # 4 B per item
+    assert fits(8, 1, 2048, 2, 2) and not fits(8, 1, 2048, 3, 2)   # 12 B per item
+    assert fits(8, 1, 1024, 4, 2) and not fits(8, 1, 8192, 2, 2) and not fits(4, 0, 256, 2, 2)
     for kb in (4, 8):  # on a GPU machine the shapes above were installed: back to the defaults
         for v in (False, True):
             sn.sn_tuning_set(kb, v)
@@ -154,8 +159,9 @@ def test_tuning_argument_errors_and_file_format(lib, tmp_path):
     assert L.sn_tuning_get(4, 0, None) == -1
     for bad in (SnTuning(256, 0xF, 160, 2, 0), SnTuning(32768, 0xF, 160, 2, 0), SnTuning(2048, 0x20, 160, 2, 0),
                 SnTuning(2048, 0xF, 8, 2, 0), SnTuning(2048, 0xF, 300, 2, 0), SnTuning(2048, 0xF, 160, 1, 0),
-                SnTuning(2048, 0xF, 160, 5, 0), SnTuning(2048, 0xF, 160, 2, 2),
-                SnTuning(8192, 0xF, 160, 4, 0), SnTuning(8192, 0xF, 160, 2, 1)):  # last two: staging too large
+                SnTuning(2048, 0xF, 160, 5, 0), SnTuning(2048, 0xF, 160, 2, 3),
+                SnTuning(8192, 0xF, 160, 4, 0), SnTuning(8192, 0xF, 160, 2, 1),   # staging too large
+                SnTuning(8192, 0xF, 160, 2, 2), SnTuning(4096, 0xF, 160, 4, 2)):  # window too large
         assert L.sn_tuning_set(4, 1, ctypes.byref(bad)) == -1
     L.sn_tune_segments.argtypes = L.sn_tune_segments.argtypes
     assert L.sn_tune_segments(None, None, None, 5, 4, None, None, None) == -1

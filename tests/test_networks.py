@@ -17,9 +17,6 @@ from paper_2002_05599_gb300.netgen import netgen
 NETJSON = os.path.join(ROOT, "paper_2002_05599_gb300", "netgen", "networks.json")
 HEADER = os.path.join(ROOT, "paper_2002_05599_gb300", "csrc", "networks_gen.h")
 
-# n -> comparators above the best-known size that this build accepts
-KNOWN_GAPS = {13: 1}
-
 
 @pytest.fixture(scope="module")
 def tables():
@@ -50,7 +47,7 @@ def test_table_size_and_depth(tables, n):
     data, nets = tables
     rec = data["networks"][str(n)]
     assert rec["size"] == len(nets[n])
-    assert rec["size"] <= netgen.BEST_KNOWN_SIZE[n] + KNOWN_GAPS.get(n, 0)
+    assert rec["size"] == netgen.BEST_KNOWN_SIZE[n]
     assert rec["depth"] == oracle.network_depth(n, nets[n])
 
 
