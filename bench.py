@@ -70,6 +70,8 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch parameters instead of autotuning each segmented workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving loop")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip config 1 (cold L2), config 2's other distributions and config 3 (i)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the float-key and long-segment measurements")
     ap.add_argument("--no-families", action="store_true",
@@ -91,7 +93,9 @@ def config_dict(sizes, scale):
         wl += f" (all sizes / 2^{scale})"
     return {"workload": wl, "sweep_arrays_per_n": sizes["sweep_count"],
             "uneven_segments": sizes["uneven_nseg"], "rss_segments": sizes["rss_nseg"],
-            "seed": 1, "l2": "inputs larger than L2; buffers restored from pristine copies between steps",
+            "seed": 1, "l2": "inputs larger than L2; buffers restored from pristine copies between steps, "
+                             "then the sweep (about 18 GB of traffic) runs before the uneven and RSS parts, so "
+                             "no part's input is still in L2 from the restore",
             "parallelism": "replicas (one independent batch per GPU)"}
 
 
@@ -400,6 +404,8 @@ def bench_ours(args, rank, world, local_rank, dist):
         result["network_families"] = bench_families(args, sn, pristine, device, dist)
     if not args.no_extras:
         result["extras"] = bench_extras(args, sn, device)
+    if not args.no_configs:
+        result["configs"] = bench_configs(args, sn, device)
     if not args.no_plain:
         result["plain_vs_batched"] = bench_plain_vs_batched(args, sn, device, dist)
     if rank == 0 and world == 1 and not args.no_serving:
@@ -571,6 +577,95 @@ def bench_extras(args, sn, device):
                                                              "gkeys_s": round(n / (ms_t * 1e-3) / 1e9, 2)}}
     del src, work, ref
     sn.check(sn.sn_check(), "extras")
+    return out
+
+
+# ------------------------------------------------ configurations ----------
+
+def bench_configs(args, sn, device):
+    """The configurations that are not parts of the step, each timed on its
+    own: config 1 with a cold L2, config 2's other three key distributions,
+    and the uneven batch with uniform 1..16 lengths (config 3 (i))."""
+    import torch
+    from paper_2002_05599_gb300 import workloads as wl
+    hbm, _ = peaks()
+    reps, warm = max(5, args.steps), max(3, args.warmup)
+    out = {}
+
+    # config 1: 2^20 arrays of 8 u32 keys, seed 1: 32 MiB, which fits in the
+    # 126 MB L2, so a 256 MiB buffer is written after the input is restored
+    # and before every timed launch
+    count = (1 << 20) >> args.scale
+    src = wl.uniform_keys_torch(count * 8, np.uint32, seed=1, device=device)
+    work = src.clone()
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=device)
+    times = []
+    for rep in range(warm + reps):
+        work.copy_(src)
+        flush.fill_(rep)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        sn.check(sn.sn_sort_fixed(work, 8), "config 1")
+        b.record()
+        b.synchronize()
+        if rep >= warm:
+            times.append(a.elapsed_time(b))
+    ms = statistics.median(times)
+    out["config1_n8_2^20_arrays_cold_l2"] = {
+        "ms": round(ms, 5), "gkeys_s": round(count * 8 / (ms * 1e-3) / 1e9, 1),
+        "frac_hbm": round(8 * count * 8 / (ms * 1e-3) / 1e9 / hbm, 4), "reps": reps,
+        "timing": "CUDA events around the one launch, median; 256 MiB written between restore and launch"}
+    del src, work, flush
+
+    # config 2: the sweep under each key distribution (uniform as in the step)
+    count = (1 << 24) >> args.scale
+    dists = {}
+    for dist in ("uniform", "fewdistinct", "presorted", "reverse"):
+        tot_ms, tot_b, worst = 0.0, 0, 1.0
+        for n in SWEEP_NS:
+            src = wl.uniform_keys_torch(count * n, np.uint32, seed=900 + n, device=device)
+            if dist == "fewdistinct":
+                src = src & 3
+            elif dist in ("presorted", "reverse"):
+                w = torch.sort(src.view(-1, n).to(torch.int64) & 0xFFFFFFFF, dim=1).values
+                if dist == "reverse":
+                    w = w.flip(1)
+                src = torch.where(w >= (1 << 31), w - (1 << 32), w).to(torch.int32).reshape(-1)
+            work = src.clone()
+            ms = _time_calls(lambda: sn.check(sn.sn_sort_fixed(work, n)), lambda: work.copy_(src), reps, warm)
+            tot_ms += ms
+            tot_b += 8 * count * n
+            worst = min(worst, 8 * count * n / (ms * 1e-3) / 1e9 / hbm)
+            del src, work
+        dists[dist] = {"ms": round(tot_ms, 4), "frac_hbm": round(tot_b / (tot_ms * 1e-3) / 1e9 / hbm, 4),
+                       "min_frac_hbm_over_n": round(worst, 4)}
+    out["config2_sweep_by_distribution"] = dists
+
+    # config 3 (i): 2^24 segments, lengths uniform 1..16, u64 keys + u32 payload
+    nseg = (1 << 24) >> args.scale
+    lens = wl.segment_lengths(nseg, "uniform", seed=1, lo=1, hi=16)
+    off = wl.offsets_from_lengths(lens)
+    total = int(off[-1])
+    d_off = torch.from_numpy(off.view(np.int32)).to(device)
+    keys = wl.uniform_keys_torch(total, np.uint64, seed=1, device=device)
+    vals = torch.arange(total, dtype=torch.int32, device=device)
+    wk, wv = keys.clone(), vals.clone()
+    tuned = "library defaults"
+    if not args.no_tune:
+        tuned = autotune(sn, wk, wv, d_off)
+
+    def restore():
+        wk.copy_(keys)
+        wv.copy_(vals)
+
+    ms = _time_calls(lambda: sn.check(sn.sn_sort_segments_u64(wk, wv, d_off)), restore, reps, warm)
+    byt = 24 * total + 4 * (nseg + 1)
+    out["config3i_uniform_1..16_u64_keys_u32_payload"] = {
+        "segments": nseg, "items": total, "ms": round(ms, 4), "gkeys_s": round(total / (ms * 1e-3) / 1e9, 2),
+        "gb_s": round(byt / (ms * 1e-3) / 1e9, 1), "frac_hbm": round(byt / (ms * 1e-3) / 1e9 / hbm, 4),
+        "launch_parameters": tuned}
+    del keys, vals, wk, wv
+    sn.check(sn.sn_check(), "configs")
     return out
 
 
@@ -886,21 +981,62 @@ def oracle_step(sample):
     return keys, time.perf_counter() - t0
 
 
-def cpu_baseline(sizes, budget_s=15.0):
-    """The oracle on one host core, on the largest 2^-shift sample of the step
-    that a probe run predicts to take at most `budget_s` seconds."""
+def _split_sample(sample, parts):
+    """The sample cut into `parts` independent pieces (array ranges; segment
+    ranges with their offsets rebased), so that several threads can run the
+    oracle on it (ctypes releases the GIL during each oracle call)."""
+    pieces = [dict() for _ in range(parts)]
+    for n in SWEEP_NS:
+        a = sample[f"sweep{n}"].reshape(-1, n)
+        for i, chunk in enumerate(np.array_split(a, parts)):
+            pieces[i][f"sweep{n}"] = chunk.reshape(-1)
+    for part in ("uneven", "rss"):
+        k, v, off = sample[part]
+        bounds = np.linspace(0, off.size - 1, parts + 1).astype(np.int64)
+        for i in range(parts):
+            s0, s1 = int(bounds[i]), int(bounds[i + 1])
+            a, b = int(off[s0]), int(off[s1])
+            pieces[i][part] = (k[a:b], None if v is None else v[a:b], (off[s0:s1 + 1] - off[s0]).astype(np.uint32))
+    return pieces
+
+
+def oracle_step_threads(pieces):
+    """oracle_step over the pieces on one thread each; (keys, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=len(pieces)) as ex:
+        keys = sum(k for k, _ in ex.map(oracle_step, pieces))
+    return keys, time.perf_counter() - t0
+
+
+def _sized_sample(sizes, budget_s, threads, shift=9):
+    """The largest 2^-shift sample that a probe predicts to take at most
+    budget_s seconds on `threads` threads."""
     import math
-    import oracle
-    oracle.build()
-    shift = 9
     sample, desc = oracle_sample(sizes, shift)
     _, probe = oracle_step(sample)
-    grow = int(math.floor(math.log2(max(1.0, budget_s / max(probe, 1e-6)))))
+    grow = int(math.floor(math.log2(max(1.0, budget_s * threads / max(probe, 1e-6)))))
     shift = max(0, shift - grow)
-    sample, desc = oracle_sample(sizes, shift)
+    return oracle_sample(sizes, shift)
+
+
+def cpu_baseline(sizes, budget_s=15.0):
+    """The oracle on the host: on one core (the paper's single-core
+    measurement), and on every core of the host (one thread per core over
+    independent pieces of the sample), each on the largest 2^-shift sample of
+    the step that a probe predicts to take at most `budget_s` seconds."""
+    import oracle
+    oracle.build()
+    sample, desc = _sized_sample(sizes, budget_s, 1)
     keys, sec = oracle_step(sample)
-    return {"value": round(keys / sec / 1e9, 5), "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-            "sample": desc, "seconds": round(sec, 3)}
+    one = {"value": round(keys / sec / 1e9, 5), "cores": 1, "sample": desc, "seconds": round(sec, 3)}
+    del sample
+    cores = os.cpu_count() or 1
+    sample, desc_all = _sized_sample(sizes, budget_s, cores)
+    keys, sec = oracle_step_threads(_split_sample(sample, cores))
+    return {"value": round(keys / sec / 1e9, 5), "unit": "Gkeys/s", "cores": cores, "kind": "oracle",
+            "sample": desc_all + f"; {cores} threads (os.cpu_count()), one per piece of the sample",
+            "seconds": round(sec, 3), "single_core": one}
 
 
 def bench_reference(args, rank, world):
@@ -908,19 +1044,22 @@ def bench_reference(args, rank, world):
     import oracle
     oracle.build()
     sizes = workload_sizes(args.scale)
+    cores = os.cpu_count() or 1
     sample, desc = oracle_sample(sizes, 10)
     _, probe = oracle_step(sample)
-    # keep the whole run (warm-up + timed) within about two minutes
+    # keep the whole run (warm-up + timed, one thread per core) within about two minutes
     shift = 10
-    while shift > 5 and probe * 2 * (args.steps + args.warmup) < 120:
+    while shift > 4 and probe * 2 * (args.steps + args.warmup) < 120 * cores:
         shift -= 1
         sample, desc = oracle_sample(sizes, shift)
         _, probe = oracle_step(sample)
+    pieces = _split_sample(sample, cores)
+    desc += f"; {cores} threads (os.cpu_count()), one per piece of the sample"
     for _ in range(args.warmup):
-        oracle_step(sample)
+        oracle_step_threads(pieces)
     times, keys = [], 0
     for _ in range(args.steps):
-        keys, sec = oracle_step(sample)
+        keys, sec = oracle_step_threads(pieces)
         times.append(sec)
     sec = statistics.mean(times)
     value = round(keys / sec / 1e9, 5)
@@ -929,7 +1068,7 @@ def bench_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": config_dict(sizes, args.scale), "impl": "reference",
-        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

@@ -187,7 +187,11 @@ typedef struct {
     int tile_stages;       /* staging depth of the network kernel: 2..4 tiles in flight per block
                               (default 2); tile_stages x tile size must fit in shared memory */
     int tile_mode;         /* network kernel: 0 = warps take work items from a task ring (default),
-                              1 = all warps of a block work through each staged tile together */
+                              1 = all warps of a block work through each staged tile together,
+                              2 = one launch without binning: every warp stages windows of
+                              consecutive segments (tile_units = items per window, 512..4096;
+                              tile_stages = windows in flight per warp, 2..4) and sorts every
+                              segment of a window itself, Register Sample Sort included */
 } sn_tuning;
 
 /* Current parameters of the current device for (key_bytes = 4 or 8, with_vals = 0 or 1). */
@@ -203,9 +207,10 @@ int sn_tuning_set(int key_bytes, int with_vals, const sn_tuning *t);
  * Autotuner: times sn_sort_segments on the caller's batch (device pointers,
  * same contract as sn_sort_segments / _u64 with key_bytes 4 / 8) under
  * candidate parameters -- a coordinate search over net_classes, (tile_units,
- * tile_stages) and rss_two_min with tile_mode 0 (tile_mode 1 only through
- * sn_tuning_set), best of three runs each, the input restored from a device
- * copy before every run -- installs the fastest set for this key type and
+ * tile_stages) and rss_two_min with tile_mode 0, then a few window shapes
+ * with tile_mode 2 (tile_mode 1 only through sn_tuning_set), best of three
+ * runs each, the input restored from a device copy before every run --
+ * installs the fastest set for this key type and
  * payload kind on the current device and copies it to `out` (may be NULL).
  * Synchronous: returns after the search; the batch is left sorted.
  * Needs device memory for one copy of keys and payload (SN_ENOMEM if not).

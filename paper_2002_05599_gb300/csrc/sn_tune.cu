@@ -6,7 +6,9 @@
 // ring tile kernel, tile_mode 0) it sweeps one
 // parameter at a time over its candidates with the others fixed (skipping
 // tile shapes whose staging does not fit in shared memory), keeps a candidate
-// only if it is more than 1% faster, and makes two passes.  Every
+// only if it is more than 1% faster, and makes two passes; then it times the
+// window kernel (tile_mode 2) over a few window shapes and, if that wins,
+// sweeps the network classes and the sample threshold once more.  Every
 // timing restores the caller's batch from a device copy, then times one
 // sn_sort_segments launch sequence with CUDA events on the caller's stream;
 // the best of three runs counts.
@@ -225,6 +227,36 @@ int tune(void* keys, uint32_t* vals, const uint32_t* offsets, uint64_t nseg, int
         const float t = time_of(c);
         if (t < 0.99f * best_t) best = c, best_t = t;
       }
+    }
+    for (int two : kTwo) {
+      if (failed || two == best.rss_two_min) continue;
+      sn::SegTuning c = best;
+      c.rss_two_min = two;
+      const float t = time_of(c);
+      if (t < 0.99f * best_t) best = c, best_t = t;
+    }
+  }
+  // The one-launch window kernel (tile_mode 2) over a few window shapes, with
+  // the classes and sample threshold found above; if it wins, those two are
+  // searched once more under it.
+  static const int kWin[][2] = {{512, 2}, {512, 3}, {1024, 2}, {1024, 3}, {2048, 2}};
+  bool window_won = false;
+  for (const auto& w : kWin) {
+    if (failed || !sn::tile_fits(key_bytes, with_vals, w[0], w[1], 2)) continue;
+    sn::SegTuning c = best;
+    c.tile_mode = 2;
+    c.tile_units = w[0];
+    c.tile_stages = w[1];
+    const float t = time_of(c);
+    if (t < 0.99f * best_t) best = c, best_t = t, window_won = true;
+  }
+  if (window_won) {
+    for (unsigned mask = 0; mask <= 0x1Fu && !failed; ++mask) {
+      sn::SegTuning c = best;
+      c.net_classes = mask;
+      if (c.net_classes == best.net_classes) continue;
+      const float t = time_of(c);
+      if (t < 0.99f * best_t) best = c, best_t = t;
     }
     for (int two : kTwo) {
       if (failed || two == best.rss_two_min) continue;
