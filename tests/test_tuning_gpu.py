@@ -105,7 +105,8 @@ def test_rss_autotuner_times_the_rss_call(restore_defaults):
     ek = oracle.sort_segments(k, None, off)[0]
     dk, d_off = to_dev(k), to_dev(off)
     params, ms = sn.sn_tune_segments(dk, None, d_off, rss_only=True)
-    assert ms > 0 and params["tile_mode"] == 0
+    # the tile kernel with the RSS kernel (mode 0) or the one-launch window kernel (mode 2)
+    assert ms > 0 and params["tile_mode"] in (0, 2)
     assert sn.sn_tuning_get(4, False) == params
     assert np.array_equal(to_host(dk, np.uint32), ek)
 
