@@ -335,6 +335,113 @@ __global__ void __launch_bounds__(kBinWarps * 32)
   }
 }
 
+// ----------------------------------------------- slot-composite networks --
+//
+// With a payload the networks run on 32-bit composites instead of (key,
+// position) items: item q of a segment becomes c_q = w_q << B | q, B the bits
+// of a slot number and w_q a (32 - B)-bit window of its order-encoded key.
+// The window ends at the highest bit in which the segment's keys differ (all
+// keys agree above it), so two composites compare like their keys whenever
+// their windows differ, and like their positions when the window holds every
+// differing bit and the keys are equal: the composite order is then exactly
+// the (key, position) order, at one 32-bit min/max per side of a
+// compare-exchange (Sec. 2.1's comparator on a derived key).  Only when the
+// differing bits are wider than the window can two different keys share a
+// window; a check of adjacent composites finds that, and the segment is then
+// sorted again, exactly, by a stable insertion sort.  Keys and payload are
+// gathered by slot after the network.
+
+template <int N>
+__host__ __device__ constexpr int slot_bits() {
+  return N <= 2 ? 1 : N <= 4 ? 2 : N <= 8 ? 3 : N <= 16 ? 4 : N <= 32 ? 5 : 6;
+}
+
+template <class K>
+__device__ __forceinline__ int high_bit(K x) {
+  if constexpr (sizeof(K) == 8)
+    return x ? 63 - __clzll(static_cast<long long>(x)) : -1;
+  else
+    return x ? 31 - __clz(static_cast<int>(x)) : -1;
+}
+
+// Shift that puts the highest differing bit at the top of a W-bit window.
+template <class K>
+__device__ __forceinline__ int window_shift(K diff, int W) {
+  const int h = high_bit(diff);
+  return h >= W ? h - (W - 1) : 0;
+}
+
+template <class K>
+__device__ __forceinline__ uint32_t window_of(K a, int sh, int W) {
+  return static_cast<uint32_t>(a >> sh) & ((1u << W) - 1u);
+}
+
+// Stable insertion sort of one segment in place in shared memory (by the
+// encoded key, payload moved along): the exact fallback of the composites.
+template <class K, bool kVals, bool kF>
+__device__ __noinline__ void insertion_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L) {
+  for (int i = 1; i < L; ++i) {
+    const K x = kbuf[p + i];
+    const K ex = key_enc<K, kF>(x);
+    const uint32_t v = kVals ? vbuf[pv + i] : 0u;
+    int j = i - 1;
+    while (j >= 0 && key_enc<K, kF>(kbuf[p + j]) > ex) {
+      kbuf[p + j + 1] = kbuf[p + j];
+      if constexpr (kVals) vbuf[pv + j + 1] = vbuf[pv + j];
+      --j;
+    }
+    kbuf[p + j + 1] = x;
+    if constexpr (kVals) vbuf[pv + j + 1] = v;
+  }
+}
+
+// One lane's segment of 2 <= L <= N items at kbuf[p..p+L), payload at
+// vbuf[pv..pv+L), sorted in place through composites.
+template <int N, class K, bool kVals, bool kF>
+__device__ __forceinline__ void slot_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L) {
+  constexpr int B = slot_bits<N>();
+  constexpr int W = 32 - B;
+  constexpr uint32_t kSlot = (1u << B) - 1u;
+  K k[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) k[q] = q < L ? key_enc<K, kF>(kbuf[p + q]) : K(0);
+  K diff = 0;
+#pragma unroll
+  for (int q = 1; q < N; ++q)
+    if (q < L) diff |= k[q] ^ k[0];
+  const int sh = window_shift(diff, W);
+  uint32_t c[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+    c[q] = (q < L ? window_of(k[q], sh, W) << B : ~kSlot) | static_cast<uint32_t>(q);
+  Net<N>::run(c);
+  if (sh > 0) {  // the window may miss differing bits: two keys may share it
+    bool tie = false;
+#pragma unroll
+    for (int q = 0; q + 1 < N; ++q) tie |= (c[q] >> B) == (c[q + 1] >> B) && (c[q + 1] & kSlot) < static_cast<uint32_t>(L);
+    if (tie) {
+      insertion_segment<K, kVals, kF>(kbuf, vbuf, p, pv, L);
+      return;
+    }
+  }
+  // the first L composites are the real items in order: gather by slot
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+    if (q < L) k[q] = kbuf[p + (c[q] & kSlot)];
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+    if (q < L) kbuf[p + q] = k[q];
+  if constexpr (kVals) {
+    uint32_t v[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+      if (q < L) v[q] = vbuf[pv + (c[q] & kSlot)];
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+      if (q < L) vbuf[pv + q] = v[q];
+  }
+}
+
 // ------------------------------------------------------ per-lane networks --
 
 // Segment of L <= N items at kbuf[p..p+L), padded with +inf to N channels
@@ -342,37 +449,7 @@ __global__ void __launch_bounds__(kBinWarps * 32)
 template <int N, class K, bool kVals, bool kF>
 __device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L) {
   if constexpr (kVals) {
-    // network on keys with positions carried; equal keys left out of position
-    // order (rare) are fixed by a second, (key, position) pass
-    KeyIdx<K> it[N];
-#pragma unroll
-    for (int q = 0; q < N; ++q)
-      it[q] = KeyIdx<K>{q < L ? key_enc<K, kF>(kbuf[p + q]) : static_cast<K>(~static_cast<K>(0)),
-                        static_cast<uint32_t>(q)};
-    Net<N>::run(it);
-    bool tie = false;
-#pragma unroll
-    for (int q = 0; q + 1 < N; ++q) tie |= tie_misordered(it[q], it[q + 1], static_cast<uint32_t>(L));
-    if (tie) {
-      using IO = ItemOf<K>;
-      typename IO::T full[N];
-#pragma unroll
-      for (int q = 0; q < N; ++q) full[q] = IO::make(it[q].k, it[q].ix);
-      Net<N>::run(full);
-#pragma unroll
-      for (int q = 0; q < N; ++q) it[q] = KeyIdx<K>{IO::key(full[q]), IO::idx(full[q])};
-    }
-    uint32_t v[N];
-#pragma unroll
-    for (int q = 0; q < N; ++q)
-      if (q < L) v[q] = vbuf[pv + it[q].ix];
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-      if (q < L) {
-        kbuf[p + q] = key_dec<K, kF>(it[q].k);
-        vbuf[pv + q] = v[q];
-      }
-    }
+    slot_segment<N, K, kVals, kF>(kbuf, vbuf, p, pv, L);
   } else {
     K k[N];
 #pragma unroll
@@ -441,46 +518,58 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
   const bool upper = pair && (lane & 1);
   const int base = upper ? 16 : 0;
   if constexpr (kVals) {
-    // network (and pair merge) on keys with positions carried; if equal keys
-    // were left out of position order anywhere in the warp (rare), every lane
-    // repeats the work on (key, position) items
-    KeyIdx<K> x[16];
+    // composites: one lane's segment (slot_segment), or a lane pair's with
+    // 5-bit slots -- the even lane holds slots 0..15, the odd lane 16..31;
+    // the pair merge exchanges one 32-bit word per item
+    if (!pair) {
+      if (active && L >= 2) slot_segment<16, K, kVals, kF>(kbuf, vbuf, p, pv, L);
+      return;
+    }
+    constexpr int B = 5, W = 27;
+    K k[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) k[q] = (active && base + q < L) ? key_enc<K, kF>(kbuf[p + base + q]) : K(0);
+    const K a0 = shfl_idx(k[0], lane & ~1);  // the segment's first key
+    K diff = 0;
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-      x[q] = KeyIdx<K>{(active && base + q < L) ? key_enc<K, kF>(kbuf[p + base + q])
-                                                : static_cast<K>(~static_cast<K>(0)),
-                       static_cast<uint32_t>(base + q)};
-    Net<16>::run(x);
-    if (pair) pair_merge(x, upper);
+      if (active && base + q < L) diff |= k[q] ^ a0;
+    diff |= shfl_xor(diff, 1);
+    const int sh = window_shift(diff, W);
+    uint32_t c[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      c[q] = ((active && base + q < L) ? window_of(k[q], sh, W) << B : ~31u) | static_cast<uint32_t>(base + q);
+    Net<16>::run(c);
+    pair_merge(c, upper);
     bool tie = false;
+    if (sh > 0) {  // two different keys may share a window: check neighbours
 #pragma unroll
-    for (int q = 0; q < 15; ++q) tie |= tie_misordered(x[q], x[q + 1], static_cast<uint32_t>(L));
-    if (pair) {  // the boundary between the even lane's last item and the odd lane's first
-      const KeyIdx<K> prev = shfl_xor(x[15], 1);
-      if (upper) tie |= tie_misordered(prev, x[0], static_cast<uint32_t>(L));
+      for (int q = 0; q < 15; ++q) tie |= (c[q] >> B) == (c[q + 1] >> B) && (c[q + 1] & 31u) < static_cast<uint32_t>(L);
     }
-    if (__any_sync(kFull, tie)) {
-      using IO = ItemOf<K>;
-      typename IO::T full[16];
+    const uint32_t prev = __shfl_xor_sync(kFull, c[15], 1);  // the even lane's last item
+    if (upper && sh > 0) tie |= (prev >> B) == (c[0] >> B) && (c[0] & 31u) < static_cast<uint32_t>(L);
+    // the pair decides together (every lane takes part in the shuffle)
+    const int partner_tie = __shfl_xor_sync(kFull, tie ? 1 : 0, 1);
+    tie = active && (tie || partner_tie != 0);
+    const bool write = active && !tie;
+    // gather by slot; both lanes of a pair gather before either writes
 #pragma unroll
-      for (int q = 0; q < 16; ++q) full[q] = IO::make(x[q].k, x[q].ix);
-      Net<16>::run(full);
-      if (pair) pair_merge(full, upper);
+    for (int q = 0; q < 16; ++q)
+      if (write && base + q < L) k[q] = kbuf[p + (c[q] & 31u)];
+    __syncwarp();
 #pragma unroll
-      for (int q = 0; q < 16; ++q) x[q] = KeyIdx<K>{IO::key(full[q]), IO::idx(full[q])};
-    }
+    for (int q = 0; q < 16; ++q)
+      if (write && base + q < L) kbuf[p + base + q] = k[q];
     uint32_t v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-      if (active && base + q < L) v[q] = vbuf[pv + x[q].ix];
+      if (write && base + q < L) v[q] = vbuf[pv + (c[q] & 31u)];
     __syncwarp();
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      if (active && base + q < L) {
-        kbuf[p + base + q] = key_dec<K, kF>(x[q].k);
-        vbuf[pv + base + q] = v[q];
-      }
-    }
+    for (int q = 0; q < 16; ++q)
+      if (write && base + q < L) vbuf[pv + base + q] = v[q];
+    if (tie && !upper) insertion_segment<K, kVals, kF>(kbuf, vbuf, p, pv, L);
   } else {
     K x[16];
 #pragma unroll
@@ -583,10 +672,10 @@ __device__ __forceinline__ void warp_bitonic_smem(const RssMem<K, kVals>& rm, in
 // net_classes bit 4): a 64-channel warp network, two items per lane
 // (warp_sort64), in place of Register Sample Sort, whose sample sort and
 // classification cost more than the whole network at this size.  With a
-// payload the items carry their positions: 4-byte keys packed with them into
-// one 64-bit word (one min/max orders both), 8-byte keys ordered by key first
-// and, only when equal keys end out of position order somewhere, once more
-// by (key, position).
+// payload, and for 8-byte keys, the network sorts 32-bit composites of a key
+// window and a 6-bit slot (see slot_segment), exact (key, position) items
+// only when two different keys share a window; keys and payload are then
+// gathered by slot.
 // kInPlace: gk / gv point into the staged copy itself (the results replace
 // the segment where it is staged), so every lane gathers its payload before
 // any lane writes.
@@ -595,32 +684,60 @@ __device__ __forceinline__ void net64_segment(const K* kbuf, const uint32_t* vbu
                                               K* gk, uint32_t* gv) {
   const int e1 = 32 + lane;
   constexpr K kTop = static_cast<K>(~static_cast<K>(0));
-  if constexpr (kVals && sizeof(K) == 8) {
-    KeyIdx<K> lo{lane < L ? key_enc<K, kF>(kbuf[p + lane]) : kTop, static_cast<uint32_t>(lane)};
-    KeyIdx<K> hi{e1 < L ? key_enc<K, kF>(kbuf[p + e1]) : kTop, static_cast<uint32_t>(e1)};
-    warp_sort64(lo, hi, lane);
-    // neighbouring slots: (lane - 1, lane) in each register, (31 of lo, 0 of hi)
-    const KeyIdx<K> lo_prev = shfl_idx(lo, (lane + 31) & 31);
-    const KeyIdx<K> hi_prev = shfl_idx(hi, (lane + 31) & 31);
-    const uint32_t real = static_cast<uint32_t>(L);
-    const bool tie = lane > 0 ? (tie_misordered(lo_prev, lo, real) || tie_misordered(hi_prev, hi, real))
-                              : tie_misordered(lo_prev, hi, real);
+  if constexpr (kVals || sizeof(K) == 8) {
+    // composites with 6-bit slots (see slot_segment); the exact fallback
+    // sorts (key, position) items through the same network
+    constexpr int B = 6, W = 26;
+    const K klo = lane < L ? key_enc<K, kF>(kbuf[p + lane]) : K(0);
+    const K khi = e1 < L ? key_enc<K, kF>(kbuf[p + e1]) : K(0);
+    const K a0 = shfl_idx(klo, 0);
+    K d = (lane < L ? klo ^ a0 : K(0)) | (e1 < L ? khi ^ a0 : K(0));
+    if constexpr (sizeof(K) == 8) {
+      const uint32_t dl = __reduce_or_sync(kFull, static_cast<uint32_t>(d));
+      const uint32_t dh = __reduce_or_sync(kFull, static_cast<uint32_t>(d >> 32));
+      d = (static_cast<K>(dh) << 32) | dl;
+    } else {
+      d = __reduce_or_sync(kFull, d);
+    }
+    const int sh = window_shift(d, W);
+    uint32_t clo = (lane < L ? window_of(klo, sh, W) << B : ~63u) | static_cast<uint32_t>(lane);
+    uint32_t chi = (e1 < L ? window_of(khi, sh, W) << B : ~63u) | static_cast<uint32_t>(e1);
+    warp_sort64(clo, chi, lane);
+    bool tie = false;
+    if (sh > 0) {  // two different keys may share a window: check neighbouring slots
+      const uint32_t lo_prev = __shfl_sync(kFull, clo, (lane + 31) & 31);
+      const uint32_t hi_prev = __shfl_sync(kFull, chi, (lane + 31) & 31);
+      auto same = [&](uint32_t x, uint32_t y) {
+        return (x >> B) == (y >> B) && (y & 63u) < static_cast<uint32_t>(L);
+      };
+      tie = lane > 0 ? (same(lo_prev, clo) || same(hi_prev, chi)) : same(lo_prev, chi);
+    }
     if (__any_sync(kFull, tie)) {
       using FI = ItemOf<K>;
-      typename FI::T a = FI::make(lo.k, lo.ix), b = FI::make(hi.k, hi.ix);
+      typename FI::T a = lane < L ? FI::make(klo, static_cast<uint32_t>(lane)) : FI::sentinel(lane);
+      typename FI::T b = e1 < L ? FI::make(khi, static_cast<uint32_t>(e1)) : FI::sentinel(e1);
       warp_sort64(a, b, lane);
-      lo = KeyIdx<K>{FI::key(a), FI::idx(a)};
-      hi = KeyIdx<K>{FI::key(b), FI::idx(b)};
+      clo = FI::idx(a);
+      chi = FI::idx(b);
+    } else {
+      clo &= 63u;
+      chi &= 63u;
     }
-    const uint32_t vlo = lane < L ? vbuf[pv + lo.ix] : 0u, vhi = e1 < L ? vbuf[pv + hi.ix] : 0u;
+    // gather by slot from the staged copy; every lane before any lane writes
+    const K olo = lane < L ? kbuf[p + clo] : K(0), ohi = e1 < L ? kbuf[p + chi] : K(0);
+    uint32_t vlo = 0, vhi = 0;
+    if constexpr (kVals) {
+      vlo = lane < L ? vbuf[pv + clo] : 0u;
+      vhi = e1 < L ? vbuf[pv + chi] : 0u;
+    }
     if constexpr (kInPlace) __syncwarp();
     if (lane < L) {
-      gk[lane] = key_dec<K, kF>(lo.k);
-      gv[lane] = vlo;
+      gk[lane] = olo;
+      if constexpr (kVals) gv[lane] = vlo;
     }
     if (e1 < L) {
-      gk[e1] = key_dec<K, kF>(hi.k);
-      gv[e1] = vhi;
+      gk[e1] = ohi;
+      if constexpr (kVals) gv[e1] = vhi;
     }
   } else {
     using IO = RssIO<K, kVals>;
@@ -678,25 +795,52 @@ __device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf,
   using IO = RssIO<K, kVals>;
   using It = typename IO::T;
   constexpr K kTop = static_cast<K>(~static_cast<K>(0));
+  const int rounds = (L + 31) >> 5;
 
-  // 1. sorted sample keys: slot q < 32 in s0 of lane q, slot 32 + q in s1 of lane q
+  // 0. keys in registers (item e = 32 r + lane).  Sample, splitters and
+  //    classification work on a 32-bit window of the encoded key: the key
+  //    itself for 4-byte keys; for 8-byte keys the 32 bits from the highest
+  //    bit in which the segment's keys differ down (every key agrees above
+  //    it, so the window's order never contradicts the key order, and a
+  //    bucket still holds a contiguous range of keys).  The buckets are then
+  //    sorted by the full key.
+  K xk[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int e = (r << 5) + lane;
+    xk[r] = (r < rounds && e < L) ? key_enc<K, kF>(kbuf[p + e]) : kTop;
+  }
+  int sh = 0;
+  if constexpr (sizeof(K) == 8) {
+    const K k0 = shfl_idx(xk[0], 0);
+    K diff = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      if (r < rounds && (r << 5) + lane < L) diff |= xk[r] ^ k0;
+    const uint32_t dl = __reduce_or_sync(kFull, static_cast<uint32_t>(diff));
+    const uint32_t dh = __reduce_or_sync(kFull, static_cast<uint32_t>(diff >> 32));
+    sh = window_shift((static_cast<K>(dh) << 32) | dl, 32);
+  }
+  auto win = [&](K x) -> uint32_t { return static_cast<uint32_t>(x >> sh); };
+
+  // 1. sorted sample windows: slot q < 32 in s0 of lane q, slot 32 + q in s1 of lane q
   const bool two = L > two_min;
   const int S = two ? 64 : 32;
-  K s0, s1 = kTop;
+  uint32_t s0, s1 = 0xFFFFFFFFu;
   {
     const int q0 = ((2 * lane + 1) * L) / (2 * S);
-    s0 = key_enc<K, kF>(kbuf[p + q0]);
+    s0 = win(key_enc<K, kF>(kbuf[p + q0]));
     warp_network32(s0, lane);
     if (two) {
       const int q1 = ((2 * (32 + lane) + 1) * L) / (2 * S);
-      s1 = key_enc<K, kF>(kbuf[p + q1]);
+      s1 = win(key_enc<K, kF>(kbuf[p + q1]));
       warp_network32(s1, lane);
       // merge two ascending halves: slot l meets slot 63 - l; the smaller
       // keys form a bitonic lower half, the larger a bitonic upper half
       // (in reversed lane order, still bitonic), each sorted by the
       // half-cleaners 16, 8, 4, 2, 1
-      const K y = shfl_idx(s1, 31 - lane);
-      K lo = pick(s0, y, true), hi = pick(s0, y, false);
+      const uint32_t y = shfl_idx(s1, 31 - lane);
+      uint32_t lo = pick(s0, y, true), hi = pick(s0, y, false);
 #pragma unroll
       for (int m = 16; m >= 1; m >>= 1) {
         const bool keep_min = lane < (lane ^ m);
@@ -710,43 +854,33 @@ __device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf,
 
   // 2. tree node t (depth d, position p_d) = splitter (2 p_d + 1) * 2^(4 - d)
   //    = sample slot a * that - 1
-  K tree;
+  uint32_t tree;
   {
     const int t = lane > 0 ? lane : 1;
     const int d = 31 - __clz(t);
     const int rank = (2 * (t - (1 << d)) + 1) << (4 - d);
     const int slot = two ? 2 * rank - 1 : rank - 1;
-    const K from0 = shfl_idx(s0, slot & 31);
+    const uint32_t from0 = shfl_idx(s0, slot & 31);
     tree = from0;
     if (two) {
-      const K from1 = shfl_idx(s1, slot & 31);
+      const uint32_t from1 = shfl_idx(s1, slot & 31);
       tree = slot >= 32 ? from1 : from0;
     }
   }
   rm.cnt[lane] = 0;
   __syncwarp();
 
-  // 3. classify the register-resident keys (item e = 32 r + lane)
-  const int rounds = (L + 31) >> 5;
-  K xk[8];
+  // 3. classify the register-resident keys by their windows: every window
+  //    descends j <- 2j + [t_j < w] five times (bucket b = j - 32 holds
+  //    s_b < w <= s_{b+1}).  The top levels have few distinct nodes: they are
+  //    broadcast once per segment and picked with selects (nodes 1..7); the
+  //    deeper levels read node j of lane j.
   int j[8];
+  uint32_t wk[8];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int e = (r << 5) + lane;
-    xk[r] = (r < rounds && e < L) ? key_enc<K, kF>(kbuf[p + e]) : kTop;
-  }
-  // The top levels have few distinct nodes: they are broadcast once per
-  // segment and picked with selects (nodes 1..7 for 4-byte keys, 1..3 for
-  // 8-byte keys); the deeper levels read node j of lane j.
-  constexpr bool kNarrow = sizeof(K) == 4;
-  const K n1 = shfl_idx(tree, 1), n2 = shfl_idx(tree, 2), n3 = shfl_idx(tree, 3);
-  K n4 = n1, n5 = n1, n6 = n1, n7 = n1;
-  if constexpr (kNarrow) {
-    n4 = shfl_idx(tree, 4);
-    n5 = shfl_idx(tree, 5);
-    n6 = shfl_idx(tree, 6);
-    n7 = shfl_idx(tree, 7);
-  }
+  for (int r = 0; r < 8; ++r) wk[r] = win(xk[r]);
+  const uint32_t n1 = shfl_idx(tree, 1), n2 = shfl_idx(tree, 2), n3 = shfl_idx(tree, 3);
+  const uint32_t n4 = shfl_idx(tree, 4), n5 = shfl_idx(tree, 5), n6 = shfl_idx(tree, 6), n7 = shfl_idx(tree, 7);
   // The descent has no branch inside: it runs over 4 or all 8 rounds (keys
   // past the segment are +inf, sink to the last bucket and are never
   // counted), so the independent rounds interleave.
@@ -754,19 +888,19 @@ __device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf,
     constexpr int R = decltype(R_)::value;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      j[r] = 2 + (n1 < xk[r] ? 1 : 0);
-      j[r] = 2 * j[r] + ((j[r] & 1 ? n3 : n2) < xk[r] ? 1 : 0);
+      j[r] = 2 + (n1 < wk[r] ? 1 : 0);
+      j[r] = 2 * j[r] + ((j[r] & 1 ? n3 : n2) < wk[r] ? 1 : 0);
     }
 #pragma unroll
     for (int lv = 2; lv < 5; ++lv) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        K t;
-        if (kNarrow && lv == 2)
+        uint32_t t;
+        if (lv == 2)  // the same on every lane (an unrolled loop index)
           t = j[r] & 2 ? (j[r] & 1 ? n7 : n6) : (j[r] & 1 ? n5 : n4);
         else
           t = shfl_idx(tree, j[r]);
-        j[r] = 2 * j[r] + (t < xk[r] ? 1 : 0);
+        j[r] = 2 * j[r] + (t < wk[r] ? 1 : 0);
       }
     }
   };

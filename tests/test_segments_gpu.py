@@ -199,3 +199,22 @@ def test_rss_range_full_size(dtype, keys):
     # 2^20 segments of 17..256 items, keys only
     k, _, off = wl.segment_batch(1 << 20, "uniform", keys, dtype, False, seed=1, lo=17, hi=256)
     _sampled_full_check("rss", k, None, off)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_segments_window_ties_take_the_exact_path(dtype):
+    # Payload sorts run their networks on composites of a key window and the
+    # item's slot.  Keys built to differ in their top bit and in their lowest
+    # bits only make two different keys share a window, so the networks' tie
+    # check must send those segments through the exact fallback; keys equal
+    # in all bits must still keep their input order.
+    rng = np.random.default_rng(51)
+    bits = 8 * np.dtype(dtype).itemsize
+    for lo, hi in ((2, 16), (17, 32), (33, 64), (2, 256)):
+        k, v, off = wl.segment_batch(20000, "uniform", "uniform", dtype, True, seed=52 + lo, lo=lo, hi=hi)
+        top = (rng.integers(0, 2, k.size).astype(np.uint64) << np.uint64(bits - 1))
+        low = rng.integers(0, 4, k.size).astype(np.uint64)
+        k = (top | low).astype(dtype)
+        for mode in ("sn", "rss"):
+            assert_parity(mode, k, v, off)
+            assert_parity(mode, k, None, off)
