@@ -70,6 +70,9 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch parameters instead of autotuning each segmented workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving loop")
+    ap.add_argument("--tuning", default="",
+                    help="parameter file: loaded if it exists (no autotuning), else written after autotuning, "
+                         "so that a profiled run uses the timed run's launch parameters")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip config 1 (cold L2), config 2's other distributions and config 3 (i)")
     ap.add_argument("--no-extras", action="store_true",
@@ -301,12 +304,18 @@ def bench_ours(args, rank, world, local_rank, dist):
     status = sn.sn_check()
     sn.check(status, "warm-up")
     tuned = {}
-    if not args.no_tune:  # autotune each segmented workload on its own batch (untimed)
+    if args.tuning and os.path.exists(args.tuning):  # the parameters a previous run tuned and saved
+        sn.check(sn.sn_tuning_load(args.tuning), "sn_tuning_load")
+        tuned = {"loaded": args.tuning,
+                 "uneven": sn.sn_tuning_get(8, True), "rss": sn.sn_tuning_get(4, False)}
+    elif not args.no_tune:  # autotune each segmented workload on its own batch (untimed)
         restore()  # on unsorted input: the warm-up left the batches sorted
         if "uneven" in parts:
             tuned["uneven"] = autotune(sn, work["uneven_keys"], work["uneven_vals"], work["uneven_off"])
         if "rss" in parts:
             tuned["rss"] = autotune(sn, work["rss_keys"], None, work["rss_off"], rss_only=True)
+        if args.tuning:
+            sn.check(sn.sn_tuning_save(args.tuning), "sn_tuning_save")
     graphs = {}
     if "uneven" in parts and not args.no_graph:
         graphs["uneven"] = capture_uneven(sn, work)

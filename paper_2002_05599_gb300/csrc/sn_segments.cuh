@@ -518,40 +518,39 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
   const bool upper = pair && (lane & 1);
   const int base = upper ? 16 : 0;
   if constexpr (kVals) {
-    // composites: one lane's segment (slot_segment), or a lane pair's with
-    // 5-bit slots -- the even lane holds slots 0..15, the odd lane 16..31;
-    // the pair merge exchanges one 32-bit word per item
-    if (!pair) {
-      if (active && L >= 2) slot_segment<16, K, kVals, kF>(kbuf, vbuf, p, pv, L);
-      return;
-    }
+    // composites (see slot_segment) with 5-bit slots, one code path for both
+    // kinds of work item: a lane's own segment (slots 0..15), or a lane
+    // pair's (the even lane slots 0..15, the odd lane 16..31, merged after
+    // the network by exchanging one 32-bit word per item)
     constexpr int B = 5, W = 27;
     K k[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) k[q] = (active && base + q < L) ? key_enc<K, kF>(kbuf[p + base + q]) : K(0);
-    const K a0 = shfl_idx(k[0], lane & ~1);  // the segment's first key
+    const K a0 = shfl_idx(k[0], pair ? (lane & ~1) : lane);  // the segment's first key
     K diff = 0;
 #pragma unroll
     for (int q = 0; q < 16; ++q)
       if (active && base + q < L) diff |= k[q] ^ a0;
-    diff |= shfl_xor(diff, 1);
+    const K partner_diff = shfl_xor(diff, 1);
+    if (pair) diff |= partner_diff;
     const int sh = window_shift(diff, W);
     uint32_t c[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q)
       c[q] = ((active && base + q < L) ? window_of(k[q], sh, W) << B : ~31u) | static_cast<uint32_t>(base + q);
     Net<16>::run(c);
-    pair_merge(c, upper);
+    if (pair) pair_merge(c, upper);
     bool tie = false;
     if (sh > 0) {  // two different keys may share a window: check neighbours
 #pragma unroll
       for (int q = 0; q < 15; ++q) tie |= (c[q] >> B) == (c[q + 1] >> B) && (c[q + 1] & 31u) < static_cast<uint32_t>(L);
     }
-    const uint32_t prev = __shfl_xor_sync(kFull, c[15], 1);  // the even lane's last item
-    if (upper && sh > 0) tie |= (prev >> B) == (c[0] >> B) && (c[0] & 31u) < static_cast<uint32_t>(L);
-    // the pair decides together (every lane takes part in the shuffle)
+    // the even lane's last item and the odd lane's first; the pair decides
+    // together (every lane takes part in both shuffles)
+    const uint32_t prev = __shfl_xor_sync(kFull, c[15], 1);
+    if (pair && upper && sh > 0) tie |= (prev >> B) == (c[0] >> B) && (c[0] & 31u) < static_cast<uint32_t>(L);
     const int partner_tie = __shfl_xor_sync(kFull, tie ? 1 : 0, 1);
-    tie = active && (tie || partner_tie != 0);
+    tie = active && (tie || (pair && partner_tie != 0));
     const bool write = active && !tie;
     // gather by slot; both lanes of a pair gather before either writes
 #pragma unroll
@@ -569,7 +568,7 @@ __device__ __forceinline__ void seg16(K* kbuf, uint32_t* vbuf, int p, int pv, in
 #pragma unroll
     for (int q = 0; q < 16; ++q)
       if (write && base + q < L) vbuf[pv + base + q] = v[q];
-    if (tie && !upper) insertion_segment<K, kVals, kF>(kbuf, vbuf, p, pv, L);
+    if (tie && !upper && L >= 2) insertion_segment<K, kVals, kF>(kbuf, vbuf, p, pv, L);
   } else {
     K x[16];
 #pragma unroll
