@@ -444,8 +444,11 @@ __device__ __forceinline__ void slot_segment(K* kbuf, uint32_t* vbuf, int p, int
 
 // ------------------------------------------------------ per-lane networks --
 
-// Segment of L <= N items at kbuf[p..p+L), padded with +inf to N channels
-// (payload at vbuf[pv..pv+L)).
+// Segment of 2 <= L <= N items at kbuf[p..p+L) (payload at vbuf[pv..pv+L)):
+// with a payload through composites (slot_segment), keys alone by the
+// network itself, padded with +inf to N channels.  (Composites for 8-byte
+// keys alone were measured slower: the gather and the extra registers cost
+// more than the 64-bit min/max they replace.)
 template <int N, class K, bool kVals, bool kF>
 __device__ __forceinline__ void net_segment(K* kbuf, uint32_t* vbuf, int p, int pv, int L) {
   if constexpr (kVals) {
