@@ -148,7 +148,7 @@ int rss_sort_segments_u64(uint64_t *keys, uint32_t *vals, const uint32_t *offset
  * running under the allocator's lock), a framework that only hands out buffers
  * it manages.  Same contract and results as sn_sort_segments_u64, with these
  * differences:
- *   - scratch is a fixed device array inside the library (about 1.2 MB per GPU
+ *   - scratch is a fixed device array inside the library (about 1.45 MB per GPU
  *     that loads the library, kept until the process exits); no cudaMalloc,
  *     cudaFree or pool allocation happens in the call;
  *   - nseg must be at most SN_NOALLOC_MAX_SEGMENTS, else SN_ERANGE (nothing

@@ -1,7 +1,8 @@
 // Device scratch of one segmented call: a plan header, the tile table, the
-// per-tile class counts (16 bytes per tile) and the per-tile index lists
-// (u16 per segment, grouped by class, Register Sample Sort entries last).
-// Every region starts on a 256-byte boundary.
+// per-tile class counts (16 bytes per tile), the per-tile index lists (u16
+// per segment, grouped by class, Register Sample Sort entries last) and the
+// segments' class bytes (one per segment, in 4-byte words aligned like the
+// offsets' 16-byte groups).  Every region starts on a 256-byte boundary.
 #pragma once
 
 #include <cstddef>
@@ -18,7 +19,7 @@ struct Plan {
 
 struct ScratchLayout {
   uint64_t cap;  // entries of the tile tables (an upper bound on tiles + 1)
-  size_t plan_at, tile_first_at, counts_at, order_at, total;
+  size_t plan_at, tile_first_at, counts_at, order_at, cls_at, total;
 
   static constexpr size_t up256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
@@ -31,7 +32,8 @@ struct ScratchLayout {
         tile_first_at(up256(sizeof(Plan))),
         counts_at(up256(tile_first_at + cap * 4)),
         order_at(up256(counts_at + cap * 16)),
-        total(up256(order_at + (nseg + 8) * 2)) {}
+        cls_at(up256(order_at + (nseg + 8) * 2)),
+        total(up256(cls_at + nseg + 8)) {}
 };
 
 }  // namespace seg

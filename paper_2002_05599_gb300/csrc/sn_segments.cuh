@@ -4,9 +4,9 @@
 // 1. seg_plan_kernel -- cuts the batch into tiles.  Segment s gets the
 //    position u_s = s + (offsets[s] - offsets[0]) and belongs to tile u_s / E,
 //    so a tile holds at most E segments and at most E + 256 items.  Every
-//    segment is validated here; bad offsets stop the call before any data is
-//    touched.
-// 2. seg_bin_kernel -- bins every tile's segments by length: the paper's
+//    segment is validated here, and classified by length (one class byte per
+//    segment); bad offsets stop the call before any data is touched.
+// 2. seg_bin_kernel -- bins every tile's segments by class: the paper's
 //    suggestion (Sec. 5) of bucketing base cases by size so that batches of
 //    identical size are solved together.  Each tile gets class counts and an
 //    index list grouped by class; segments for Register Sample Sort (33+
@@ -203,46 +203,123 @@ struct RssWarpLayout {
 
 // ---------------------------------------------------------------- plan -----
 
+// Position p = s + a of segment s, a = (address of offsets / 4) mod 4: the
+// offsets are read in aligned 16-byte groups, group g holding the offsets of
+// positions 4g .. 4g + 3, and the segment classes are written one byte per
+// position, a 4-byte word per group.  A group's 16 bytes never leave the
+// 16-byte granule of an offset that exists, so reading the unused part of the
+// first and last groups cannot fault.
+__device__ __forceinline__ int plan_shift(const uint32_t* offsets) {
+  return static_cast<int>((reinterpret_cast<uintptr_t>(offsets) & 15) / 4);
+}
+
+// Tile of position u (u < 2^33: a segment index plus an item offset) for
+// tiles of E = m 2^k units, m odd: u >> k for m = 1; for m = 3 (E = 3072,
+// 6144, 12288; k >= 8, so u >> k fits 32 bits) a multiply-high by the
+// rounded-up 2^33 / 3, exact for every 32-bit dividend; else u / E.
+struct TileDiv {
+  int k;
+  uint32_t m, E;
+  __device__ __forceinline__ uint32_t operator()(uint64_t u) const {
+    if (m == 1) return static_cast<uint32_t>(u >> k);
+    if (m == 3) return __umulhi(static_cast<uint32_t>(u >> k), 0xAAAAAAABu) >> 1;
+    return static_cast<uint32_t>(u / E);
+  }
+};
+
+constexpr int kPlanU = 4;
+
+// One thread per group (grid-stride over whole warps): validates every
+// segment, records the first segment of every tile, and writes each
+// segment's class byte (seg_class of its length; kSkipCls past the batch).
+// Groups whose four segments all exist and precede the last one take a
+// 32-bit path; the others (the batch's two ends) the general one.
 __global__ void __launch_bounds__(256)
-    seg_plan_kernel(const uint32_t* __restrict__ offsets, uint64_t nseg, uint32_t E, int e_shift, Plan* plan,
-                    uint32_t* __restrict__ tile_first, uint64_t tile_cap, unsigned* status) {
-  // tile of position u: u / E, a shift when E is a power of two (e_shift >= 0)
-  auto tile_of = [&](uint64_t u) -> uint64_t { return e_shift >= 0 ? u >> e_shift : u / E; };
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    seg_plan_kernel(const uint32_t* __restrict__ offsets, uint64_t nseg, TileDiv tile_of, Plan* plan,
+                    uint32_t* __restrict__ tile_first, uint64_t tile_cap, uint32_t* __restrict__ cls, bool rss_only,
+                    uint32_t net_mask, unsigned* status) {
+  __shared__ uint8_t cls_of[34];
+  if (threadIdx.x < 34) cls_of[threadIdx.x] = static_cast<uint8_t>(seg_class(threadIdx.x, rss_only, net_mask));
+  __syncthreads();
+  const int a = plan_shift(offsets);
+  const uint4* ov = reinterpret_cast<const uint4*>(offsets - a);
   const uint32_t base = offsets[0];
+  const int lane = threadIdx.x & 31;
+  // groups covering offsets[0 .. nseg]
+  const uint64_t ngroups = (nseg + static_cast<uint64_t>(a)) / 4 + 1;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   bool bad = false;
-  // kPlanU segments per thread and step (s, s + stride, ...), their offset
-  // loads issued together
-  constexpr int kPlanU = 4;
-  for (uint64_t sb = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; sb < nseg;
-       sb += kPlanU * stride) {
-    uint32_t o[kPlanU], o1[kPlanU], op[kPlanU];
+  // kPlanU runs of 32 groups per warp and step (run u: groups g0 + 32 u +
+  // lane), their loads issued together
+  for (uint64_t gw = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u)) * kPlanU;
+       gw < ngroups; gw += stride * kPlanU) {
+    uint4 vv[kPlanU];
 #pragma unroll
     for (int u = 0; u < kPlanU; ++u) {
-      const uint64_t s = sb + u * stride;
-      o[u] = o1[u] = op[u] = 0;
-      if (s < nseg) {
-        o[u] = offsets[s];
-        o1[u] = offsets[s + 1];
-        if (s > 0) op[u] = offsets[s - 1];
+      const uint64_t g = gw + 32 * u + lane;
+      vv[u] = g < ngroups ? ov[g] : make_uint4(0u, 0u, 0u, 0u);
+    }
+    // the offsets just before and just after the step's groups
+    const int64_t lo_i = static_cast<int64_t>(4 * gw) - a - 1;
+    const int64_t hi_i = static_cast<int64_t>(4 * (gw + 32 * kPlanU)) - a;
+    const uint32_t edge_lo = lo_i >= 0 ? offsets[lo_i] : 0u;
+    const uint32_t edge_hi = hi_i <= static_cast<int64_t>(nseg) ? offsets[hi_i] : 0u;
+#pragma unroll
+    for (int u = 0; u < kPlanU; ++u) {
+    const uint64_t g = gw + 32 * u + lane;
+    const bool in = g < ngroups;
+    const uint4 v = vv[u];
+    // the offset after the group's last position and the one before its first
+    // (across runs from the neighbouring run, across steps from the edges)
+    uint32_t nx = __shfl_down_sync(kFull, v.x, 1);
+    uint32_t pw = __shfl_up_sync(kFull, v.w, 1);
+    const uint32_t nx31 = u + 1 < kPlanU ? __shfl_sync(kFull, vv[u + 1 < kPlanU ? u + 1 : u].x, 0) : edge_hi;
+    const uint32_t pw0 = u > 0 ? __shfl_sync(kFull, vv[u > 0 ? u - 1 : 0].w, 31) : edge_lo;
+    if (lane == 31) nx = nx31;
+    if (lane == 0) pw = pw0;
+    const int64_t first = static_cast<int64_t>(4 * g) - a;  // segment of position 4g
+    const uint32_t o[6] = {pw, v.x, v.y, v.z, v.w, nx};
+    uint32_t word = 0;
+    if (in && first >= 1 && first + 5 <= static_cast<int64_t>(nseg)) {
+      const uint64_t f = static_cast<uint64_t>(first);
+      uint32_t tp = tile_of(f - 1 + (pw - base));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t o0 = o[k + 1], o1 = o[k + 2];
+        const uint32_t len = o1 - o0;
+        bad |= o1 < o0 || len > kMaxSeg || o0 < base;
+        word |= static_cast<uint32_t>(cls_of[min(len, 33u)]) << (8 * k);
+        const uint32_t t = tile_of(f + k + (o0 - base));
+        if (t != tp && t < tile_cap) tile_first[t] = static_cast<uint32_t>(f + k);
+        tp = t;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t sk = first + k;
+        uint32_t c = kSkipCls;
+        if (in && sk >= 0 && sk < static_cast<int64_t>(nseg)) {
+          const uint64_t sq = static_cast<uint64_t>(sk);
+          const uint32_t o0 = o[k + 1], o1 = o[k + 2], op = o[k];
+          const uint32_t len = o1 - o0;
+          if (o1 < o0 || len > kMaxSeg || o0 < base) bad = true;
+          c = cls_of[len < 33u ? len : 33u];
+          const uint64_t t = tile_of(sq + static_cast<uint64_t>(o0 - base));
+          const uint64_t tp = sq > 0 ? tile_of((sq - 1) + static_cast<uint64_t>(op - base)) : ~0ull;
+          if (t != tp && t < tile_cap) tile_first[t] = static_cast<uint32_t>(sq);
+          if (sq == nseg - 1) {
+            if (t + 1 < tile_cap) {
+              tile_first[t + 1] = static_cast<uint32_t>(nseg);
+              plan->ntiles = static_cast<unsigned>(t + 1);
+            } else {
+              bad = true;
+            }
+          }
+        }
+        word |= c << (8 * k);
       }
     }
-#pragma unroll
-    for (int u = 0; u < kPlanU; ++u) {
-      const uint64_t s = sb + u * stride;
-      if (s >= nseg) break;
-      if (o1[u] < o[u] || o1[u] - o[u] > kMaxSeg || o[u] < base) bad = true;
-      const uint64_t t = tile_of(s + static_cast<uint64_t>(o[u] - base));
-      const uint64_t tp = s > 0 ? tile_of((s - 1) + static_cast<uint64_t>(op[u] - base)) : ~0ull;
-      if (t != tp && t < tile_cap) tile_first[t] = static_cast<uint32_t>(s);
-      if (s == nseg - 1) {
-        if (t + 1 < tile_cap) {
-          tile_first[t + 1] = static_cast<uint32_t>(nseg);
-          plan->ntiles = static_cast<unsigned>(t + 1);
-        } else {
-          bad = true;
-        }
-      }
+    if (in) cls[g] = word;
     }
   }
   if (bad) {
@@ -253,83 +330,116 @@ __global__ void __launch_bounds__(256)
 
 // ----------------------------------------------------------------- bin -----
 
-// One warp per tile (grid-stride over warps): counts[8t + c] for the tile
-// classes c and counts[8t + 6] for Register Sample Sort, and the tile-local
-// indices of its segments grouped by class in order[s0 .. s1).  A segment's
-// class comes from a per-block table indexed by min(length, 33).  Counting:
-// each lane sets a one-byte field for its class (classes 0..3 in one word,
-// 4..7 in another) and one warp-wide add per word sums a chunk of 32
-// segments.  Placing: lanes of one class find each other with a match, and a
-// segment's position is its class's running total (per-warp shared memory)
-// plus its rank among them.  Both passes classify kBinChunks chunks of 32
-// segments at a time, so that their offset loads are in flight together.
-constexpr int kBinChunks = 4;
+// One warp per tile (grid-stride over warps), reading the class bytes of the
+// tile's segments, four per lane (one word) and 128 per warp step:
+// counts[8t + c] for the tile classes c and counts[8t + 6] for Register
+// Sample Sort, and the tile-local indices of its segments grouped by class
+// (classes in hand-out order, RSS last; any order inside a class) in
+// order[s0 .. s1).  Each class has a one-byte field of a 64-bit word; a
+// lane's four bytes give its fields, and a warp-wide add per half word sums
+// a step.  Placing: an inclusive warp scan of the lanes' field words gives
+// every lane, per class, the entries of the lanes before it; a segment's
+// place is its class's running start (per-warp shared memory) plus that plus
+// its rank among the lane's own bytes.  (Fields never carry: a step adds at
+// most 128 to one.)
 constexpr int kBinWarps = 8;
+constexpr int kBinU = 4;  // warp steps whose loads are issued together
 __global__ void __launch_bounds__(kBinWarps * 32)
-    seg_bin_kernel(const uint32_t* __restrict__ offsets, const Plan* plan, const uint32_t* __restrict__ tile_first,
-                   uint16_t* __restrict__ counts, uint16_t* __restrict__ order, bool rss_only,
-                   uint32_t net_mask) {
+    seg_bin_kernel(const uint32_t* __restrict__ cls, const uint32_t* __restrict__ offsets, const Plan* plan,
+                   const uint32_t* __restrict__ tile_first, uint16_t* __restrict__ counts,
+                   uint16_t* __restrict__ order) {
   constexpr int kCls = kNumTileCls + 1;  // tile classes + RSS; kSkipCls (= kCls) is not listed
   static_assert(kSkipCls == 7, "eight class fields");
-  __shared__ uint8_t cls_of[34];
   __shared__ uint32_t cur_s[kBinWarps][8];
-  if (threadIdx.x < 34) cls_of[threadIdx.x] = static_cast<uint8_t>(seg_class(threadIdx.x, rss_only, net_mask));
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   uint32_t* cur = cur_s[threadIdx.x >> 5];
   const unsigned ntiles = plan->bad ? 0u : plan->ntiles;
   const unsigned W = gridDim.x * kBinWarps;
-  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t a = static_cast<uint32_t>(plan_shift(offsets));
+  // a word's four class bytes, those outside positions [p0, p1) set to kSkipCls
+  auto load = [&](uint32_t wi, uint32_t p0, uint32_t p1, uint32_t w1) -> uint32_t {
+    uint32_t w = wi < w1 ? cls[wi] : 0x07070707u;
+    if (4 * wi < p0 || 4 * wi + 4 > p1) {  // the tile's first or last word
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t p = 4 * wi + k;
+        if (p < p0 || p >= p1) w |= 7u << (8 * k);
+      }
+    }
+    return w;
+  };
+  auto fields = [](uint32_t w) -> uint64_t {
+    uint64_t f = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f += 1ull << (8 * ((w >> (8 * k)) & 7u));
+    return f;
+  };
   for (unsigned t = blockIdx.x * kBinWarps + (threadIdx.x >> 5); t < ntiles; t += W) {
     const uint32_t s0 = tile_first[t], s1 = tile_first[t + 1];
-    const uint32_t ns = s1 - s0;
-    auto classify = [&](uint32_t i0, int (&c)[kBinChunks]) {
+    const uint32_t p0 = s0 + a, p1 = s1 + a;
+    const uint32_t w0 = p0 / 4, w1 = (p1 + 3) / 4;
+    uint32_t tot[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    for (uint32_t wb = w0; wb < w1; wb += 32 * kBinU) {
+      uint32_t ws[kBinU];  // kBinU steps' loads in flight together
 #pragma unroll
-      for (int u = 0; u < kBinChunks; ++u) {
-        const uint32_t i = i0 + 32u * u + lane;
-        const uint32_t len = i < ns ? offsets[s0 + i + 1] - offsets[s0 + i] : 0u;
-        c[u] = i < ns ? cls_of[len < 33u ? len : 33u] : kSkipCls;
-      }
-    };
-    // counts in 16-bit fields: acc[0] classes 0, 1; acc[1] 2, 3; acc[2] 4, 5; acc[3] 6, 7
-    uint32_t acc[4] = {0u, 0u, 0u, 0u};
-    for (uint32_t i0 = 0; i0 < ns; i0 += 32u * kBinChunks) {
-      int c[kBinChunks];
-      classify(i0, c);
+      for (int u = 0; u < kBinU; ++u) ws[u] = load(wb + 32 * u + lane, p0, p1, w1);
 #pragma unroll
-      for (int u = 0; u < kBinChunks; ++u) {
-        const uint32_t bit = 1u << ((c[u] & 3) * 8);
-        const uint32_t a = __reduce_add_sync(kFull, c[u] < 4 ? bit : 0u);
-        const uint32_t b = __reduce_add_sync(kFull, c[u] >= 4 ? bit : 0u);
-        acc[0] += __byte_perm(a, 0u, 0x4140);
-        acc[1] += __byte_perm(a, 0u, 0x4342);
-        acc[2] += __byte_perm(b, 0u, 0x4140);
-        acc[3] += __byte_perm(b, 0u, 0x4342);
+      for (int u = 0; u < kBinU; ++u) {
+        if (wb + 32 * u >= w1) break;  // warp-uniform
+        const uint64_t f = fields(ws[u]);
+        const uint32_t lo = __reduce_add_sync(kFull, static_cast<uint32_t>(f));
+        const uint32_t hi = __reduce_add_sync(kFull, static_cast<uint32_t>(f >> 32));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          tot[q] += (lo >> (8 * q)) & 0xFFu;
+          tot[4 + q] += (hi >> (8 * q)) & 0xFFu;
+        }
       }
     }
     uint32_t at = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const uint32_t n = (acc[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
       if (lane == q) {
         cur[q] = at;
-        counts[8ull * t + q] = static_cast<uint16_t>(q < kCls ? n : 0u);
+        counts[8ull * t + q] = static_cast<uint16_t>(q < kCls ? tot[q] : 0u);
       }
-      at += n;
+      at += tot[q];
     }
     __syncwarp();
-    for (uint32_t i0 = 0; i0 < ns; i0 += 32u * kBinChunks) {
-      int c[kBinChunks];
-      classify(i0, c);
+    for (uint32_t wb0 = w0; wb0 < w1; wb0 += 32 * kBinU) {
+      uint32_t ws[kBinU];
 #pragma unroll
-      for (int u = 0; u < kBinChunks; ++u) {
-        const uint32_t i = i0 + 32u * u + lane;
-        const unsigned m = __match_any_sync(kFull, c[u]);
-        const uint32_t below = m & lt;
-        if (c[u] < kCls) order[s0 + cur[c[u]] + __popc(below)] = static_cast<uint16_t>(i);
-        __syncwarp();
-        if (below == 0) cur[c[u]] += __popc(m);
-        __syncwarp();
+      for (int u = 0; u < kBinU; ++u) ws[u] = load(wb0 + 32 * u + lane, p0, p1, w1);
+#pragma unroll
+      for (int u = 0; u < kBinU; ++u) {
+      if (wb0 + 32 * u >= w1) break;  // warp-uniform
+      const uint32_t wi = wb0 + 32 * u + lane;
+      const uint32_t w = ws[u];
+      const uint64_t f = fields(w);
+      uint32_t slo = static_cast<uint32_t>(f), shi = static_cast<uint32_t>(f >> 32);
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t ylo = __shfl_up_sync(kFull, slo, d), yhi = __shfl_up_sync(kFull, shi, d);
+        if (lane >= d) {
+          slo += ylo;
+          shi += yhi;
+        }
+      }
+      const uint32_t tlo = __shfl_sync(kFull, slo, 31), thi = __shfl_sync(kFull, shi, 31);
+      // entries before this byte: the lanes below, then the lane's own earlier bytes
+      uint64_t run = ((static_cast<uint64_t>(shi) << 32) | slo) - f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t c = (w >> (8 * k)) & 7u;
+        if (c < static_cast<uint32_t>(kCls)) {
+          const uint32_t rank = static_cast<uint32_t>(run >> (8 * c)) & 0xFFu;
+          order[s0 + cur[c] + rank] = static_cast<uint16_t>(4 * wi + k - p0);
+        }
+        run += 1ull << (8 * c);
+      }
+      __syncwarp();
+      if (lane < 8) cur[lane] += ((lane < 4 ? tlo : thi) >> ((lane & 3) * 8)) & 0xFFu;
+      __syncwarp();
       }
     }
   }
@@ -827,16 +937,16 @@ __device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf,
 
   // 1. sorted sample windows: slot q < 32 in s0 of lane q, slot 32 + q in s1 of lane q
   const bool two = L > two_min;
-  const int S = two ? 64 : 32;
   uint32_t s0, s1 = 0xFFFFFFFFu;
   {
-    const int q0 = ((2 * lane + 1) * L) / (2 * S);
-    s0 = win(key_enc<K, kF>(kbuf[p + q0]));
-    warp_network32(s0, lane);
-    if (two) {
-      const int q1 = ((2 * (32 + lane) + 1) * L) / (2 * S);
-      s1 = win(key_enc<K, kF>(kbuf[p + q1]));
-      warp_network32(s1, lane);
+    // slot q of a*32 sits at position floor((2q + 1) L / (2 a 32))
+    const int sh2 = two ? 7 : 6;
+    s0 = win(key_enc<K, kF>(kbuf[p + (((2 * lane + 1) * L) >> sh2)]));
+    if (!two) {
+      warp_network32(s0, lane);
+    } else {
+      s1 = win(key_enc<K, kF>(kbuf[p + (((2 * (32 + lane) + 1) * L) >> sh2)]));
+      warp_network32x2(s0, s1, lane);
       // merge two ascending halves: slot l meets slot 63 - l; the smaller
       // keys form a bitonic lower half, the larger a bitonic upper half
       // (in reversed lane order, still bitonic), each sorted by the
@@ -908,8 +1018,12 @@ __device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf,
   };
 #pragma unroll
   for (int r = 0; r < 8; ++r) j[r] = 32;
-  if (rounds <= 4)
+  if (rounds <= 2)
+    descend(std::integral_constant<int, 2>{});
+  else if (rounds <= 4)
     descend(std::integral_constant<int, 4>{});
+  else if (rounds <= 6)
+    descend(std::integral_constant<int, 6>{});
   else
     descend(std::integral_constant<int, 8>{});
   uint32_t rank_in[8];
@@ -1837,18 +1951,23 @@ cudaError_t launch_all(K* keys, uint32_t* vals, const uint32_t* offsets, uint64_
   uint32_t* tile_first = reinterpret_cast<uint32_t*>(base + sl.tile_first_at);
   uint16_t* counts = reinterpret_cast<uint16_t*>(base + sl.counts_at);
   uint16_t* order = reinterpret_cast<uint16_t*>(base + sl.order_at);
+  uint32_t* cls = reinterpret_cast<uint32_t*>(base + sl.cls_at);
 
   cudaError_t e = cudaMemsetAsync(plan, 0, sizeof(Plan), stream);
   if (e != cudaSuccess) return e;
-  const uint64_t want = (nseg + 255) / 256;
-  const unsigned g1 = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(want, 16ull * d.sm_count)));
-  const int e_shift = (E & (E - 1)) == 0 ? __builtin_ctz(E) : -1;
-  seg_plan_kernel<<<g1, 256, 0, stream>>>(offsets, nseg, E, e_shift, plan, tile_first, sl.cap, d.status);
+  // a thread per group of four offsets, kPlanU groups per step; at most one
+  // wave of 8 blocks per SM
+  const uint64_t want = (nseg / 4 + 2 + 256 * kPlanU - 1) / (256 * kPlanU);
+  const unsigned g1 = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(want, 8ull * d.sm_count)));
+  TileDiv tdiv{__builtin_ctz(E), 0, E};
+  tdiv.m = E >> tdiv.k;
+  if (tdiv.m == 3 && tdiv.k < 8) tdiv.m = 0;  // keep u >> k within 32 bits: the general division
+  seg_plan_kernel<<<g1, 256, 0, stream>>>(offsets, nseg, tdiv, plan, tile_first, sl.cap, cls, rss_only,
+                                          tun.net_classes, d.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const unsigned g2 = static_cast<unsigned>(std::max<uint64_t>(
       1, std::min<uint64_t>(sl.cap - 1, 8ull * d.sm_count)));
-  seg_bin_kernel<<<g2, kBinWarps * 32, 0, stream>>>(offsets, plan, tile_first, counts, order, rss_only,
-                                          tun.net_classes);
+  seg_bin_kernel<<<g2, kBinWarps * 32, 0, stream>>>(cls, offsets, plan, tile_first, counts, order);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   if (tun.tile_mode == 1) {
