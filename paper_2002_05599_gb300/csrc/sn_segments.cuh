@@ -368,10 +368,14 @@ __global__ void __launch_bounds__(kBinWarps * 32)
     }
     return w;
   };
-  auto fields = [](uint32_t w) -> uint64_t {
+  // one-byte class fields: fld[c] = 1 << 8c
+  __shared__ uint64_t fld[8];
+  if (threadIdx.x < 8) fld[threadIdx.x] = 1ull << (8 * threadIdx.x);
+  __syncthreads();
+  auto fields = [&](uint32_t w) -> uint64_t {
     uint64_t f = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) f += 1ull << (8 * ((w >> (8 * k)) & 7u));
+    for (int k = 0; k < 4; ++k) f += fld[(w >> (8 * k)) & 7u];
     return f;
   };
   for (unsigned t = blockIdx.x * kBinWarps + (threadIdx.x >> 5); t < ntiles; t += W) {
@@ -391,8 +395,8 @@ __global__ void __launch_bounds__(kBinWarps * 32)
         const uint32_t hi = __reduce_add_sync(kFull, static_cast<uint32_t>(f >> 32));
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          tot[q] += (lo >> (8 * q)) & 0xFFu;
-          tot[4 + q] += (hi >> (8 * q)) & 0xFFu;
+          tot[q] += __byte_perm(lo, 0u, 0x4440 + q);
+          tot[4 + q] += __byte_perm(hi, 0u, 0x4440 + q);
         }
       }
     }
@@ -426,16 +430,20 @@ __global__ void __launch_bounds__(kBinWarps * 32)
         }
       }
       const uint32_t tlo = __shfl_sync(kFull, slo, 31), thi = __shfl_sync(kFull, shi, 31);
-      // entries before this byte: the lanes below, then the lane's own earlier bytes
-      uint64_t run = ((static_cast<uint64_t>(shi) << 32) | slo) - f;
+      // entries before a byte: its class's field of the lanes below, plus
+      // the lane's own earlier bytes of that class
+      const uint64_t ex = ((static_cast<uint64_t>(shi) << 32) | slo) - f;
+      const uint32_t elo = static_cast<uint32_t>(ex), ehi = static_cast<uint32_t>(ex >> 32);
+      uint32_t c[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c[k] = (w >> (8 * k)) & 7u;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const uint32_t c = (w >> (8 * k)) & 7u;
-        if (c < static_cast<uint32_t>(kCls)) {
-          const uint32_t rank = static_cast<uint32_t>(run >> (8 * c)) & 0xFFu;
-          order[s0 + cur[c] + rank] = static_cast<uint16_t>(4 * wi + k - p0);
-        }
-        run += 1ull << (8 * c);
+        uint32_t rank = __byte_perm(elo, ehi, c[k]) & 0xFFu;
+#pragma unroll
+        for (int k2 = 0; k2 < k; ++k2) rank += c[k2] == c[k] ? 1u : 0u;
+        if (c[k] < static_cast<uint32_t>(kCls))
+          order[s0 + cur[c[k]] + rank] = static_cast<uint16_t>(4 * wi + k - p0);
       }
       __syncwarp();
       if (lane < 8) cur[lane] += ((lane < 4 ? tlo : thi) >> ((lane & 3) * 8)) & 0xFFu;
