@@ -85,13 +85,16 @@ def test_segments_every_length(mode, dtype):
 
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
 @pytest.mark.parametrize("net64", [True, False])
-def test_segments_33_to_64(dtype, net64):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_segments_33_to_64(dtype, net64, mode):
     # segments of 33..64 items: 64-channel warp network (net_classes bit 4) or
-    # Register Sample Sort; many keys equal to the maximum (the padding value)
-    # and many ties
+    # Register Sample Sort, after either tile kernel (mode 0 ring, mode 1
+    # synchronous); many keys equal to the maximum (the padding value) and
+    # many ties; a few short and long segments mixed in
     kb = np.dtype(dtype).itemsize
     rng = np.random.default_rng(21)
-    lens = np.repeat(np.arange(33, 65, dtype=np.uint32), 40)
+    lens = np.concatenate([np.repeat(np.arange(33, 65, dtype=np.uint32), 40),
+                           np.array([0, 1, 5, 16, 17, 32, 65, 200, 256] * 5, dtype=np.uint32)])
     rng.shuffle(lens)
     off = wl.offsets_from_lengths(lens)
     total = int(off[-1])
@@ -101,7 +104,7 @@ def test_segments_33_to_64(dtype, net64):
     v = np.arange(total, dtype=np.uint32)
     try:
         for with_vals in (True, False):
-            sn.check(sn.sn_tuning_set(kb, with_vals, net_classes=0x1F if net64 else 0xF), "set")
+            sn.check(sn.sn_tuning_set(kb, with_vals, net_classes=0x1F if net64 else 0xF, tile_mode=mode), "set")
             assert_parity("sn", k, v if with_vals else None, off)
     finally:
         for with_vals in (True, False):
