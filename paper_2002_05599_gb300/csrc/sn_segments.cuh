@@ -748,16 +748,28 @@ __device__ __forceinline__ void bucket_network(const RssMem<K, kVals>& rm, int s
   }
 }
 
+// The network for the warp's largest bucket m <= 16: 4, 8, 12 or 16 channels
+// for 4-byte keys; for 8-byte keys only 8 or 16 (their networks' code is
+// twice as large, and with four sizes the warps, each in a different one,
+// missed the instruction cache more than the smaller networks saved: u64 RSS
+// range 2.02 -> 1.92 ms, while the same change made u32 2 % slower).
 template <class K, bool kVals>
 __device__ __forceinline__ void bucket_network_class(int m, const RssMem<K, kVals>& rm, int st, int c) {
-  if (m <= 4)
-    bucket_network<4, K, kVals>(rm, st, c);
-  else if (m <= 8)
-    bucket_network<8, K, kVals>(rm, st, c);
-  else if (m <= 12)
-    bucket_network<12, K, kVals>(rm, st, c);
-  else
-    bucket_network<16, K, kVals>(rm, st, c);
+  if constexpr (sizeof(K) == 8) {
+    if (m <= 8)
+      bucket_network<8, K, kVals>(rm, st, c);
+    else
+      bucket_network<16, K, kVals>(rm, st, c);
+  } else {
+    if (m <= 4)
+      bucket_network<4, K, kVals>(rm, st, c);
+    else if (m <= 8)
+      bucket_network<8, K, kVals>(rm, st, c);
+    else if (m <= 12)
+      bucket_network<12, K, kVals>(rm, st, c);
+    else
+      bucket_network<16, K, kVals>(rm, st, c);
+  }
 }
 
 
@@ -901,7 +913,7 @@ __device__ __forceinline__ void net64_segment(const K* kbuf, const uint32_t* vbu
 //  4. bucket starts by a warp scan (lane b owns bucket b);
 //  5. scatter the (key, position) items into the shared item buffer;
 //  6. lane b sorts bucket b with a network padded to the warp's largest bucket
-//     of at most 16 items (4, 8, 12 or 16 channels); buckets above 16 items
+//     of at most 16 items (4, 8, 12 or 16 channels; 8 or 16 for 8-byte keys); buckets above 16 items
 //     (rare unless keys repeat) are sorted by the whole warp (32-lane network,
 //     or a bitonic pass in shared memory above 32);
 //  7. write back (payload gathered by original position).
@@ -1003,7 +1015,9 @@ __device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf,
   const uint32_t n4 = shfl_idx(tree, 4), n5 = shfl_idx(tree, 5), n6 = shfl_idx(tree, 6), n7 = shfl_idx(tree, 7);
   // The descent has no branch inside: it runs over 4 or all 8 rounds (keys
   // past the segment are +inf, sink to the last bucket and are never
-  // counted), so the independent rounds interleave.
+  // counted), so the independent rounds interleave.  (Descents over 2, 4, 6
+  // or 8 rounds did fewer instructions but ran 4 % slower: two more unrolled
+  // copies in the instruction working set.)
   auto descend = [&](auto R_) {
     constexpr int R = decltype(R_)::value;
 #pragma unroll
@@ -1026,12 +1040,8 @@ __device__ __forceinline__ void rss_segment(const K* kbuf, const uint32_t* vbuf,
   };
 #pragma unroll
   for (int r = 0; r < 8; ++r) j[r] = 32;
-  if (rounds <= 2)
-    descend(std::integral_constant<int, 2>{});
-  else if (rounds <= 4)
+  if (rounds <= 4)
     descend(std::integral_constant<int, 4>{});
-  else if (rounds <= 6)
-    descend(std::integral_constant<int, 6>{});
   else
     descend(std::integral_constant<int, 8>{});
   uint32_t rank_in[8];
