@@ -137,28 +137,38 @@ def test_segments_all_empty_and_single():
 
 
 @pytest.mark.parametrize("mode", ["sn", "rss"])
-def test_segments_misaligned_pointers(mode):
-    # keys/vals/offsets one element past a 16-byte boundary
-    k, v, off = wl.segment_batch(3000, "geometric", "uniform", np.uint64, True, seed=12)
-    pad_k = to_dev(np.concatenate([np.zeros(1, np.uint64), k]))
-    pad_v = to_dev(np.concatenate([np.zeros(1, np.uint32), v]))
-    pad_o = to_dev(np.concatenate([np.zeros(1, np.uint32), off]))
-    fn = CALLS[(mode, np.uint64)]
-    sn.check(fn(pad_k.data_ptr() + 8, pad_v.data_ptr() + 4, pad_o.data_ptr() + 4, off.size - 1))
-    sn.check(sn.sn_check())
-    ref_k, ref_v = oracle.sort_segments(k, v, off)
-    assert np.array_equal(to_host(pad_k, np.uint64)[1:], ref_k)
-    assert np.array_equal(to_host(pad_v, np.uint32)[1:], ref_v)
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_segments_misaligned_pointers(mode, shift):
+    # keys / vals / offsets `shift` elements past a 16-byte boundary (the plan
+    # kernel reads the offsets in aligned 16-byte groups), batches whose last
+    # group is cut at every position, and batches of a few segments (only the
+    # general path of the plan kernel)
+    for nseg in (1, 2, 3, 5, 3000, 3001, 3002, 3003):
+        k, v, off = wl.segment_batch(nseg, "geometric", "uniform", np.uint64, True, seed=12 + nseg)
+        pad_k = to_dev(np.concatenate([np.zeros(shift, np.uint64), k]))
+        pad_v = to_dev(np.concatenate([np.zeros(shift, np.uint32), v]))
+        pad_o = to_dev(np.concatenate([np.zeros(shift, np.uint32), off]))
+        fn = CALLS[(mode, np.uint64)]
+        sn.check(fn(pad_k.data_ptr() + 8 * shift, pad_v.data_ptr() + 4 * shift, pad_o.data_ptr() + 4 * shift,
+                    off.size - 1))
+        sn.check(sn.sn_check())
+        ref_k, ref_v = oracle.sort_segments(k, v, off)
+        assert np.array_equal(to_host(pad_k, np.uint64)[shift:], ref_k)
+        assert np.array_equal(to_host(pad_v, np.uint32)[shift:], ref_v)
 
 
 def test_segments_bad_offsets_leave_data_untouched():
-    for lens_bad in ("long", "decreasing"):
+    for lens_bad in ("long", "decreasing", "first", "last"):
         k, v, off = wl.segment_batch(2000, "uniform", "uniform", np.uint32, True, seed=8)
         off = off.astype(np.int64)
         if lens_bad == "long":
             off[1000:] += 300  # segment 999 gets 300+ items
-        else:
+        elif lens_bad == "decreasing":
             off[700] = off[699] - 1  # segment 699 gets a negative length
+        elif lens_bad == "first":
+            off[1:] += 300  # segment 0 (the batch's first offsets group)
+        else:
+            off[-1] += 300  # the last segment (the batch's last group)
         off = off.astype(np.uint32)
         tk, tv, to_ = to_dev(k), to_dev(v), to_dev(off)
         assert sn.sn_sort_segments(tk, tv, to_) == sn.SN_OK  # detected on the device
