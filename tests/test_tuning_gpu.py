@@ -16,7 +16,12 @@ SETS = [dict(tile_units=512, net_classes=0x0, rss_two_min=16, tile_stages=2, til
         dict(tile_units=1024, net_classes=0x15, rss_two_min=64, tile_stages=4, tile_mode=0),
         dict(tile_units=2048, net_classes=0xA, rss_two_min=200, tile_stages=3, tile_mode=1),
         dict(tile_units=512, net_classes=0x14, rss_two_min=128, tile_stages=3, tile_mode=1),
-        dict(tile_units=1024, net_classes=0x0, rss_two_min=160, tile_stages=4, tile_mode=1)]
+        dict(tile_units=1024, net_classes=0x0, rss_two_min=160, tile_stages=4, tile_mode=1),
+        # tile sizes that are neither a power of two nor 3 * 2^k: the plan
+        # kernel's general tile division (and 3 * 2^k, its multiply-high path)
+        dict(tile_units=1000, net_classes=0x1F, rss_two_min=160, tile_stages=2, tile_mode=0),
+        dict(tile_units=1537, net_classes=0x1F, rss_two_min=160, tile_stages=2, tile_mode=1),
+        dict(tile_units=1536, net_classes=0x1F, rss_two_min=160, tile_stages=2, tile_mode=0)]
 
 
 @pytest.fixture
