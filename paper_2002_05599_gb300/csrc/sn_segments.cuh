@@ -216,7 +216,9 @@ __device__ __forceinline__ int plan_shift(const uint32_t* offsets) {
 // Tile of position u (u < 2^33: a segment index plus an item offset) for
 // tiles of E = m 2^k units, m odd: u >> k for m = 1; for m = 3 (E = 3072,
 // 6144, 12288; k >= 8, so u >> k fits 32 bits) a multiply-high by the
-// rounded-up 2^33 / 3, exact for every 32-bit dividend; else u / E.
+// rounded-up 2^33 / 3, exact for every 32-bit dividend (division by an
+// invariant integer through multiplication, Granlund and Montgomery); else
+// u / E.
 struct TileDiv {
   int k;
   uint32_t m, E;
@@ -913,9 +915,9 @@ __device__ __forceinline__ void net64_segment(const K* kbuf, const uint32_t* vbu
 //  4. bucket starts by a warp scan (lane b owns bucket b);
 //  5. scatter the (key, position) items into the shared item buffer;
 //  6. lane b sorts bucket b with a network padded to the warp's largest bucket
-//     of at most 16 items (4, 8, 12 or 16 channels; 8 or 16 for 8-byte keys); buckets above 16 items
-//     (rare unless keys repeat) are sorted by the whole warp (32-lane network,
-//     or a bitonic pass in shared memory above 32);
+//     of at most 16 items (4, 8, 12 or 16 channels; 8 or 16 for 8-byte keys);
+//     buckets above 16 items (rare unless keys repeat) are sorted by the whole
+//     warp (32-lane network, or a bitonic pass in shared memory above 32);
 //  7. write back (payload gathered by original position).
 //  kInPlace: gk / gv point into the staged copy itself; the payload words are
 //  then parked in the item buffer first and written once every lane has
